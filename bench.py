@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark: AMGF-PCG seconds to a relative preconditioned residual of 1e-8 on one GB300.
+
+Workload (default): the c64 two-block contact system -- two stacked Q1 linear-elastic
+blocks of 64x64x32 elements each (E=1, nu=0.3), node-to-node normal contact on the
+65x65 interface (m=4225), barrier diagonal D log-uniform in [1e-2, 1e8], n=811,200
+DOFs, three seeded right-hand sides (seeds 0, 1, 2) cycled over the steps.  Synthetic
+data from contactgen (seeded); FP64 arithmetic throughout.
+
+One step = one full AMGF-PCG solve (x0 = 0) through the C ABI with inputs resident in
+HBM.  The working set (fine operator ~0.76 GB plus hierarchy) is larger than L2, so
+no flush is needed between steps.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amgf|reference] [--config c64]
+
+--impl reference times the CPU FP64 oracle on the host cores on a bounded sample of
+the same workload (a few PCG iterations per step, scaled to the full solve's
+iteration count).  Under torchrun with N > 1 the GPU arm runs N independent replicas
+(the solve does not shard; no collective on the data path); the reference arm runs
+on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AMGF-PCG seconds to 1e-8 rel. residual"
+WORKLOADS = {
+    "c64": "two-block Q1 elasticity, 64x64x32 elements per block, n=811200, m=4225 node-to-node contact rows, "
+           "D log-uniform [1e-2,1e8], 3 seeded RHS, FP64 AMGF-PCG",
+    "tiny": "two-block Q1 elasticity, 8x8x4 elements per block, n=1944, m=81, D log-uniform [1e-2,1e4]",
+    "c96": "two-block Q1 elasticity, 96x96x48 elements per block, n=2709792, m=9409, D log-uniform [1e-2,1e10], "
+           "FP64 AMGF-PCG",
+    "c160": "two-block Q1 elasticity, 160x160x80 elements per block, n=12442080, m=25921, D log-uniform "
+            "[1e-2,1e12], FP64 AMGF-PCG",
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.bus_id and self.bus_id.lower() not in parts[1].lower():
+                    continue
+                rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(config: str):
+    import contactgen as cg
+    p = cg.make_problem(config, seed=0)
+    c = cg.CONFIGS[config]
+    rhs = [cg.draw_D_b(s, p.m, p.n, c["d_lo"], c["d_hi"])[1] for s in (0, 1, 2)]
+    return p, rhs
+
+
+def cpu_oracle_sample(p, rhs, iters_full: float, sample_iters: int, reps: int = 1):
+    """Time `sample_iters` oracle PCG iterations (after its setup); scale to a full solve."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle(p.K, p.J, p.D)
+    t_setup = time.perf_counter() - t0
+    per_iter = []
+    for k in range(reps):
+        t0 = time.perf_counter()
+        o.pcg(rhs[k % len(rhs)], tol=1e-30, maxit=sample_iters)
+        per_iter.append((time.perf_counter() - t0) / sample_iters)
+    sec_iter = statistics.median(per_iter)
+    o.close()
+    return sec_iter * iters_full, sec_iter, t_setup
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    p, rhs = make_inputs(args.config)
+    cores = os.cpu_count()
+    o = oracle.Oracle(p.K, p.J, p.D)
+    # iteration count of the full solve (untimed, once): scales the per-iteration sample
+    _, k_full, st, *_ = o.pcg(rhs[0], tol=1e-8)
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o.pcg(rhs[step % 3], tol=1e-30, maxit=args.ref_iters)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt / args.ref_iters * k_full)
+    value = statistics.mean(times)
+    sample = (f"{args.ref_iters} PCG iterations of the {args.config} solve per step (oracle setup excluded), "
+              f"scaled by the full solve's {k_full} iterations")
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.config}: {WORKLOADS.get(args.config, args.config)}", "rtol": 1e-8,
+                       "stop": "sqrt(r^T z / r0^T z0)", "parallelism": "host cores (OpenMP row loops)"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_2505_18576_gb300 as amgf
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = dist_
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    p, rhs = make_inputs(args.config)
+    t0 = time.perf_counter()
+    s = amgf.Solver(p.K, p.J, p.D)
+    t_setup = time.perf_counter() - t0
+    info = s.info
+    n = p.n
+    bdev = [torch.from_numpy(b).cuda() for b in rhs]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(args.warmup):
+        x.zero_()
+        s.pcg_solve(bdev[k % 3], x)
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+    sampler = ClockSampler(None if bus is None else str(bus))
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, launches, solve_s = [], 0, []
+    ev0.record(stream)
+    for k in range(args.steps):
+        x.zero_()
+        st = s.pcg_solve(bdev[k % 3], x, stream=stream)
+        iters.append(st.iters)
+        launches += st.kernel_launches
+        solve_s.append(st.t_solve_s)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    bh = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        xh[:] = 0.0
+        s.pcg_solve_host(bh[k % 3], xh)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # dominant kernel: fine-level l1-Jacobi post-smoother (level-0 SpMV + fused epilogue)
+    kms, kbytes = s.time_kernel(1, warmup=5, reps=50)
+    peak, peak_kind = peaks()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            tr = json.load(f)
+        if tr.get("config") == args.config and tr.get("kernel_source_sha") == kernel_source_sha():
+            traffic = tr.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            est, sec_iter, t_orc_setup = cpu_oracle_sample(p, rhs, float(np.mean(iters)), args.cpu_iters)
+            cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"{args.cpu_iters} oracle PCG iterations on the {args.config} system (setup "
+                             f"excluded, {t_orc_setup:.1f}s), {sec_iter * 1e3:.1f} ms/iteration scaled by the "
+                             f"GPU solve's mean {np.mean(iters):.1f} iterations"}
+        value = ms * 1e-3
+        line = {
+            "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.config}: {WORKLOADS.get(args.config, args.config)}",
+                       "n": n, "m": p.m, "nc": int(info.nc), "levels": int(info.nlevels),
+                       "op_complexity": round(float(info.op_complexity), 4), "rtol": 1e-8,
+                       "stop": "sqrt(r^T z / r0^T z0)", "pcg_iters": iters,
+                       "l2": "working set larger than L2 (no flush)", "setup_s": round(t_setup, 3),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "csr_kernel<32,POST> level 0 (l1-Jacobi sweep, A_0 = S)",
+                         "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_kind": f"{peak_kind} (burst)"},
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("kernels.cuh", "amgf.cu"):
+        with open(os.path.join(ROOT, "paper_2505_18576_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="amgf", choices=["amgf", "reference"])
+    ap.add_argument("--config", default="c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations timed for cpu_baseline")
+    ap.add_argument("--ref-iters", type=int, default=4, help="oracle PCG iterations per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * amgf.h -- C ABI of the GB300 AMGF-PCG library.
+ *
+ * Solves the condensed interior-point Newton system
+ *     A u = b,   A = K + J^T D J                       (Section 3, eq. linsystem1)
+ * by preconditioned conjugate gradients with the AMGF preconditioner
+ *     I - M A = (I - B A)(I - P A_w^{-1} P^T A)(I - B A),  A_w = P^T A P
+ * (Section 5.1, Definition "AMGF"), where B is one classical AMG V-cycle built
+ * from A (Remark after Lemma "condition number estimate": B := AMG(A) with l1
+ * smoothers) and P is the natural embedding of the contact DOFs
+ * I_c = nonzero columns of J (Section 4 and Section 5.1).
+ *
+ * The hierarchy setup (coarsening, Galerkin products, I_c and the factorisation
+ * of A_w) runs on the host.  Every step of amgf_apply and amgf_pcg_solve runs
+ * in this library's sm_103a CUDA kernels; there is no CPU fallback: without a
+ * CUDA device every call that touches the device returns AMGF_ERR_CUDA.
+ *
+ * Conventions for every entry point:
+ *   - Return value: an amgf_status code; 0 = success.  No call throws or aborts
+ *     across the ABI.  amgf_last_error() gives a message for the calling thread.
+ *   - Host arrays are read during the call only; the caller keeps ownership.
+ *   - Device pointers (suffix _dev) are caller-owned, 8-byte aligned, of the
+ *     stated length, on the device that was current at amgf_setup.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work is
+ *     ordered after prior work on `stream`, and later work on `stream` sees its
+ *     results; the library runs it on its own stream joined by events.
+ *   - A handle is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef AMGF_H
+#define AMGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AMGF_OK = 0,
+  AMGF_ERR_INVALID_ARG = 1,  /* null pointer, bad size, unsorted or out-of-range CSR index */
+  AMGF_ERR_NONFINITE = 2,    /* NaN/Inf in D, b or in a PCG scalar */
+  AMGF_ERR_NOT_SPD = 3,      /* D_r <= 0, non-positive pivot in the coarse or filter factor */
+  AMGF_ERR_BREAKDOWN = 4,    /* p^T A p <= 0 or r^T z <= 0 during PCG */
+  AMGF_ERR_NOT_CONVERGED = 5,/* maxit reached; x holds the last iterate */
+  AMGF_ERR_CUDA = 6,         /* CUDA runtime error or no device */
+  AMGF_ERR_OOM = 7           /* device or host allocation failed */
+} amgf_status;
+
+/* Host CSR matrix: row_ptr[nrows+1] (int64, row_ptr[0] = 0), col_idx[nnz] (int32,
+ * strictly ascending within a row, 0 <= col < ncols), val[nnz] (float64). */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+} amgf_csr;
+
+typedef struct {
+  double strength_theta;  /* AMG strength threshold (0.8) */
+  double rtol;            /* PCG stop: sqrt(r^T z / r0^T z0) < rtol (1e-8); Section 4 uses this norm */
+  int max_levels;         /* AMG levels including the coarsest (25) */
+  int max_coarse;         /* stop coarsening at n_l <= max_coarse (128); coarsest solved exactly */
+  int num_functions;      /* unknowns per node for the unknown approach (3); DOF i has function i % 3 */
+  int nu;                 /* l1-Jacobi sweeps before and after the coarse correction (1) */
+  int filter;             /* 1: AMGF (default); 0: plain AMG V-cycle, M = B */
+  int contact_components; /* 0: I_c = nonzero columns of J; 1: all num_functions DOFs of those nodes;
+                             2: all DOFs (P = I, test) */
+  int maxit;              /* PCG iteration cap (5000, Section 6.1) */
+  int use_graph;          /* 1: capture the PCG loop in one CUDA graph with a device-side while node */
+  int verbose;            /* 1: print setup summary to stderr */
+} amgf_options;
+
+typedef struct {
+  int iters;              /* PCG iterations (A p products) */
+  int converged;          /* 1 if the stop test was met */
+  int status;             /* amgf_status of the solve */
+  int nlevels;
+  double rel_res_precond; /* final sqrt(r^T z / r0^T z0) */
+  double rz0;             /* r0^T z0 */
+  double t_solve_s;       /* device time of the solve (CUDA events) */
+  int64_t kernel_launches;/* this library's kernels executed by the solve */
+} amgf_stats;
+
+typedef struct {
+  int64_t n, m, nc;          /* DOFs, constraints, |I_c| */
+  int nlevels;
+  int64_t level_rows[32];
+  int64_t level_nnz[32];     /* nnz(A_l) */
+  int64_t interp_nnz[32];    /* nnz(P_l), l < nlevels-1 */
+  int64_t filter_block;      /* block size of the block-tridiagonal A_w factor */
+  int64_t filter_nblocks;
+  double op_complexity;      /* sum nnz(A_l) / nnz(A_0) */
+  double t_setup_s;          /* host setup wall time */
+} amgf_info;
+
+typedef struct amgf_ctx* amgf_handle;
+
+/* Fill *o with the defaults listed above. */
+int amgf_options_default(amgf_options* o);
+
+/* Build the solver for A = K + J^T D J (Section 3, eq. linsystem1).
+ * K: n x n SPD stiffness (host CSR).  J: m x n contact Jacobian (host CSR), may
+ * have m = 0 (then I_c is empty).  D: host array of m positive finite values.
+ * o: options (NULL = defaults).  On success *out owns all device memory. */
+int amgf_setup(const amgf_csr* K, const amgf_csr* J, const double* D,
+               const amgf_options* o, amgf_handle* out);
+
+/* Host-only variant of amgf_setup: runs the whole host setup (A, the AMG hierarchy, I_c
+ * and the A_w factor) without touching any CUDA device.  The handle only serves
+ * amgf_get_info, amgf_export_matrix, amgf_export_contact_set, amgf_update_D and
+ * amgf_destroy; every device call on it returns AMGF_ERR_INVALID_ARG. */
+int amgf_setup_host(const amgf_csr* K, const amgf_csr* J, const double* D,
+                    const amgf_options* o, amgf_handle* out);
+
+/* New interior-point iterate: same K and J, new barrier diagonal D (host, length m).
+ * Across IP iterations only D changes (Section 4); B := AMG(A) is rebuilt for the new A. */
+int amgf_update_D(amgf_handle h, const double* D);
+
+/* z_dev = M r_dev, one AMGF application (Definition "AMGF"): y1 = B r; r1 = r - A y1;
+ * y2 = y1 + P A_w^{-1} P^T r1; r2 = r1 - A P (A_w^{-1} P^T r1); z = y2 + B r2.
+ * With filter = 0: z = B r.  Both vectors have length n.  r_dev and z_dev must not alias. */
+int amgf_apply(amgf_handle h, const double* r_dev, double* z_dev, void* stream);
+
+/* x_dev = B r_dev, one V-cycle from a zero start (the B of Section 5.1). */
+int amgf_vcycle(amgf_handle h, const double* r_dev, double* x_dev, void* stream);
+
+/* y_dev = A x_dev with A = K + J^T D J. */
+int amgf_matvec(amgf_handle h, const double* x_dev, double* y_dev, void* stream);
+
+/* w_dev = A_w^{-1} v_dev with A_w = A[I_c, I_c] (Section 5.1); v, w of length nc in
+ * ascending-DOF order of I_c. */
+int amgf_filter_solve(amgf_handle h, const double* v_dev, double* w_dev, void* stream);
+
+/* PCG on A x = b (x_dev holds x0 on entry, the solution on exit), preconditioned by
+ * M, stopped when sqrt(r^T z / r0^T z0) < rtol (Section 4) or after maxit
+ * iterations.  Synchronises `stream` to fill *st (may be NULL).
+ * Returns AMGF_ERR_NOT_CONVERGED when maxit is reached. */
+int amgf_pcg_solve(amgf_handle h, const double* b_dev, double* x_dev, amgf_stats* st, void* stream);
+
+/* Same as amgf_pcg_solve with host arrays (length n): copies b and x0 to the device,
+ * solves, copies x back.  Blocking. */
+int amgf_pcg_solve_host(amgf_handle h, const double* b_host, double* x_host, amgf_stats* st);
+
+/* Hierarchy and sizes. */
+int amgf_get_info(amgf_handle h, amgf_info* info);
+
+/* Host copy of a hierarchy matrix (tests).  which: 0 = A_l, 1 = P_l, 2 = R_l.
+ * With row_ptr == NULL only *nrows, *ncols, *nnz are written. */
+int amgf_export_matrix(amgf_handle h, int which, int level, int64_t* nrows, int64_t* ncols, int64_t* nnz,
+                       int64_t* row_ptr, int32_t* col_idx, double* val);
+
+/* Host copy of I_c (length nc, ascending DOF indices). */
+int amgf_export_contact_set(amgf_handle h, int64_t* ic);
+
+/* Time `reps` back-to-back launches of one kernel of the solve phase on `stream`
+ * with CUDA events, after `warmup` untimed launches.  which: 0 = fine-level
+ * A x (SpMV of level 0), 1 = fine-level post-smoother.  *ms = average per launch;
+ * *bytes = algorithmic bytes one launch moves (values + indices + vectors). */
+int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* stream,
+                     double* ms, double* bytes);
+
+/* Free all device and host memory of the handle. */
+int amgf_destroy(amgf_handle h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* amgf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGF_H */

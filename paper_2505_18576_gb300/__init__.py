@@ -1,0 +1,315 @@
+"""GB300 AMGF-PCG: Python binding of the C ABI in include/amgf.h.
+
+Argument marshalling only: every step of the solve runs in libamgf.so's CUDA
+kernels.  Device vectors are passed as torch CUDA tensors (float64, contiguous)
+or raw integer device pointers; PyTorch is used for device memory and streams.
+There is no CPU fallback: importing works without a GPU, but every call that
+needs the device raises AmgfError when libamgf.so cannot reach one.
+
+Function names are those of the C ABI (amgf_setup, amgf_apply, amgf_pcg_solve,
+...); ``Solver`` is a small object wrapper around a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH, build as _build
+
+__all__ = ["AmgfError", "Options", "Stats", "Info", "Solver", "load_library", "amgf_options_default",
+           "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec", "amgf_filter_solve",
+           "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
+           "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED"]
+
+EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec",
+            "amgf_filter_solve", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info",
+            "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
+            "amgf_last_error"]
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "NOT_SPD", 4: "BREAKDOWN", 5: "NOT_CONVERGED",
+          6: "CUDA", 7: "OOM"}
+
+
+class AmgfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("strength_theta", ctypes.c_double), ("rtol", ctypes.c_double),
+                ("max_levels", ctypes.c_int), ("max_coarse", ctypes.c_int), ("num_functions", ctypes.c_int),
+                ("nu", ctypes.c_int), ("filter", ctypes.c_int), ("contact_components", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
+                ("nlevels", ctypes.c_int), ("rel_res_precond", ctypes.c_double), ("rz0", ctypes.c_double),
+                ("t_solve_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("nc", ctypes.c_int64), ("nlevels", ctypes.c_int),
+                ("level_rows", ctypes.c_int64 * 32), ("level_nnz", ctypes.c_int64 * 32),
+                ("interp_nnz", ctypes.c_int64 * 32), ("filter_block", ctypes.c_int64),
+                ("filter_nblocks", ctypes.c_int64), ("op_complexity", ctypes.c_double),
+                ("t_setup_s", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libamgf.so (compiling it in place when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build()
+    if not os.path.exists(_LIB_PATH):
+        raise AmgfError(6, f"{_LIB_PATH} is missing: build it with paper_2505_18576_gb300.build.build()")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "amgf_options_default": [vp],
+        "amgf_setup": [vp, vp, vp, vp, vp],
+        "amgf_setup_host": [vp, vp, vp, vp, vp],
+        "amgf_update_D": [vp, vp],
+        "amgf_apply": [vp, vp, vp, vp],
+        "amgf_vcycle": [vp, vp, vp, vp],
+        "amgf_matvec": [vp, vp, vp, vp],
+        "amgf_filter_solve": [vp, vp, vp, vp],
+        "amgf_pcg_solve": [vp, vp, vp, vp, vp],
+        "amgf_pcg_solve_host": [vp, vp, vp, vp],
+        "amgf_get_info": [vp, vp],
+        "amgf_export_matrix": [vp, i32, i32, vp, vp, vp, vp, vp, vp],
+        "amgf_export_contact_set": [vp, vp],
+        "amgf_time_kernel": [vp, i32, i32, i32, vp, vp, vp],
+        "amgf_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = i32
+    lib.amgf_last_error.argtypes = []
+    lib.amgf_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def amgf_last_error() -> str:
+    return load_library().amgf_last_error().decode()
+
+
+def _check(st: int):
+    if st != 0:
+        raise AmgfError(st, amgf_last_error())
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    """Device or host pointer of a torch tensor / numpy array / int."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_vec(t, n: int, name: str):
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise AmgfError(1, f"{name}: expected a contiguous float64 CUDA tensor")
+    if t.numel() != n:
+        raise AmgfError(1, f"{name}: expected {n} entries, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def amgf_options_default(**overrides) -> Options:
+    o = Options()
+    _check(load_library().amgf_options_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _csr(mat, keep: list) -> Csr:
+    rp = np.ascontiguousarray(mat.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(mat.col_idx, dtype=np.int32)
+    v = np.ascontiguousarray(mat.val, dtype=np.float64)
+    keep += [rp, ci, v]
+    ncols = getattr(mat, "ncols", None)
+    if ncols is None:
+        ncols = mat.shape[1]
+    return Csr(len(rp) - 1, int(ncols), int(rp[-1]), rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+
+
+def amgf_setup(K, J=None, D=None, opts: Options | None = None, host_only: bool = False) -> ctypes.c_void_p:
+    """Host CSR K (n x n), J (m x n, optional), D (m) -> handle (c_void_p).
+
+    host_only=True calls amgf_setup_host (hierarchy only, no device)."""
+    lib = load_library()
+    keep: list = []
+    k = _csr(K, keep)
+    j = _csr(J, keep) if J is not None else None
+    d = np.ascontiguousarray(D, dtype=np.float64) if D is not None else None
+    h = ctypes.c_void_p()
+    fn = lib.amgf_setup_host if host_only else lib.amgf_setup
+    _check(fn(ctypes.byref(k), ctypes.byref(j) if j is not None else None,
+                          _ptr(d) if d is not None else None, ctypes.byref(opts) if opts else None,
+                          ctypes.byref(h)))
+    return h
+
+
+def amgf_update_D(h, D):
+    d = np.ascontiguousarray(D, dtype=np.float64)
+    _check(load_library().amgf_update_D(h, _ptr(d)))
+
+
+def amgf_apply(h, r, z, n: int, stream=None):
+    _check(load_library().amgf_apply(h, _dev_vec(r, n, "r"), _dev_vec(z, n, "z"), _stream(stream)))
+
+
+def amgf_vcycle(h, r, x, n: int, stream=None):
+    _check(load_library().amgf_vcycle(h, _dev_vec(r, n, "r"), _dev_vec(x, n, "x"), _stream(stream)))
+
+
+def amgf_matvec(h, x, y, n: int, stream=None):
+    _check(load_library().amgf_matvec(h, _dev_vec(x, n, "x"), _dev_vec(y, n, "y"), _stream(stream)))
+
+
+def amgf_filter_solve(h, v, w, nc: int, stream=None):
+    _check(load_library().amgf_filter_solve(h, _dev_vec(v, nc, "v"), _dev_vec(w, nc, "w"), _stream(stream)))
+
+
+def amgf_pcg_solve(h, b, x, n: int, stream=None, check: bool = True) -> Stats:
+    st = Stats()
+    rc = load_library().amgf_pcg_solve(h, _dev_vec(b, n, "b"), _dev_vec(x, n, "x"), ctypes.byref(st),
+                                       _stream(stream))
+    if check and rc not in (0,):
+        _check(rc)
+    st.rc = rc
+    return st
+
+
+def amgf_pcg_solve_host(h, b: np.ndarray, x: np.ndarray, check: bool = True) -> Stats:
+    assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+    st = Stats()
+    rc = load_library().amgf_pcg_solve_host(h, _ptr(b), _ptr(x), ctypes.byref(st))
+    if check and rc != 0:
+        _check(rc)
+    st.rc = rc
+    return st
+
+
+def amgf_get_info(h) -> Info:
+    info = Info()
+    _check(load_library().amgf_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def amgf_export_matrix(h, which: int, level: int):
+    """(row_ptr, col_idx, val, shape) of A_l (which=0), P_l (1) or R_l (2)."""
+    lib = load_library()
+    nr, nc, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.amgf_export_matrix(h, which, level, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(nnz),
+                                  None, None, None))
+    rp = np.empty(nr.value + 1, np.int64); ci = np.empty(nnz.value, np.int32); v = np.empty(nnz.value)
+    _check(lib.amgf_export_matrix(h, which, level, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(nnz),
+                                  _ptr(rp), _ptr(ci), _ptr(v)))
+    return rp, ci, v, (nr.value, nc.value)
+
+
+def amgf_export_contact_set(h, nc: int) -> np.ndarray:
+    out = np.empty(max(nc, 1), np.int64)
+    _check(load_library().amgf_export_contact_set(h, _ptr(out)))
+    return out[:nc]
+
+
+def amgf_time_kernel(h, which: int, warmup: int, reps: int, stream=None):
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().amgf_time_kernel(h, which, warmup, reps, _stream(stream), ctypes.byref(ms),
+                                           ctypes.byref(by)))
+    return ms.value, by.value
+
+
+def amgf_destroy(h):
+    if h:
+        load_library().amgf_destroy(h)
+
+
+class Solver:
+    """Owns one handle.  K, J: CSR objects with row_ptr/col_idx/val (contactgen.CSR works)."""
+
+    def __init__(self, K, J=None, D=None, host_only=False, **opts):
+        self.opts = amgf_options_default(**opts)
+        self.h = amgf_setup(K, J, D, self.opts, host_only=host_only)
+        self.info = amgf_get_info(self.h)
+        self.n = int(self.info.n)
+        self.nc = int(self.info.nc)
+
+    def close(self):
+        if getattr(self, "h", None):
+            amgf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update_D(self, D):
+        amgf_update_D(self.h, D)
+        self.info = amgf_get_info(self.h)
+
+    def apply(self, r, z, stream=None):
+        amgf_apply(self.h, r, z, self.n, stream)
+
+    def vcycle(self, r, x, stream=None):
+        amgf_vcycle(self.h, r, x, self.n, stream)
+
+    def matvec(self, x, y, stream=None):
+        amgf_matvec(self.h, x, y, self.n, stream)
+
+    def filter_solve(self, v, w, stream=None):
+        amgf_filter_solve(self.h, v, w, self.nc, stream)
+
+    def pcg_solve(self, b, x, stream=None, check=True) -> Stats:
+        return amgf_pcg_solve(self.h, b, x, self.n, stream, check)
+
+    def pcg_solve_host(self, b, x, check=True) -> Stats:
+        return amgf_pcg_solve_host(self.h, b, x, check)
+
+    def export(self, which: int, level: int):
+        import scipy.sparse as sp
+        rp, ci, v, shape = amgf_export_matrix(self.h, which, level)
+        return sp.csr_matrix((v, ci, rp), shape=shape)
+
+    def contact_set(self):
+        return amgf_export_contact_set(self.h, self.nc)
+
+    def time_kernel(self, which: int, warmup: int = 3, reps: int = 20, stream=None):
+        return amgf_time_kernel(self.h, which, warmup, reps, stream)

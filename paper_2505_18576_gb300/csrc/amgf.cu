@@ -1,0 +1,772 @@
+// AMGF-PCG solve phase on one GPU and the C ABI of include/amgf.h.
+//
+// Device layout (one handle):
+//   level l: A_l (CSR, int64 row pointers, int32 columns, FP64 values), P_l, R_l = P_l^T,
+//            W_l = 1 / l1_l, and four n_l-vectors (rhs, x, residual, output);
+//   coarsest: dense inverse of A_L (FP64);
+//   filter:   block-tridiagonal LDL^T factor of A_w (G_i, G_i^T, D_i^{-1}, nb x nb each),
+//             factor-position -> DOF map, and A[:, I_c] on the rows that touch I_c;
+//   PCG:      x, r, z, p, q, apply scratch (y1, r1), device scalars (PcgState).
+// One AMGF application (Definition "AMGF", Section 5.1):
+//   y1 = B r  ->  r1 = r - A y1  ->  w = A_w^{-1} P^T r1,  y1 += P w  ->  r1 -= A P w
+//   ->  z = y1 + B r1
+// where only the rows of A that touch I_c take part in r1 -= A P w.  The PCG loop runs
+// as one CUDA graph whose body sits in a device-side while node, so a solve makes no
+// host round trip until it ends.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/amgf.h"
+#include "kernels.cuh"
+#include "setup.h"
+
+namespace amgf {
+
+thread_local std::string g_last_error;
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? AMGF_ERR_OOM : AMGF_ERR_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    }                                                                                         \
+  } while (0)
+
+struct DCSR {
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  int64_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* v = nullptr;
+  int K = 4;  // lanes per row
+};
+
+struct DLevel {
+  DCSR A, P, R;
+  double* winv = nullptr;
+  double *rhs = nullptr, *x = nullptr, *res = nullptr, *out = nullptr;
+  int64_t n = 0;
+};
+
+struct Ctx {
+  amgf_options o{};
+  int device = 0;
+  int num_sms = 148;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+  // host copies kept for amgf_update_D and exports
+  HCSR Kh, Jh;
+  Hierarchy H;
+  Filter F;
+  amgf_info info{};
+  // device
+  std::vector<void*> allocs;
+  std::vector<DLevel> L;
+  double* coarse_inv = nullptr;
+  int64_t nL = 0;
+  double *fG = nullptr, *fGT = nullptr, *fDinv = nullptr, *fy = nullptr, *fz = nullptr, *fw = nullptr, *fv = nullptr;
+  int64_t* fgidx = nullptr;
+  int64_t* ficidx = nullptr;  // factor position -> index into I_c
+  int64_t* ftouch = nullptr;
+  DCSR fSc;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *y1 = nullptr, *r1 = nullptr;
+  double* partial = nullptr;
+  unsigned* counter = nullptr;
+  double* scratch_scalar = nullptr;
+  PcgState* st = nullptr;
+  PcgState* st_host = nullptr;  // pinned
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond{};
+  int64_t n = 0, m = 0;
+  bool host_only = false;
+  int64_t launches = 0;       // kernels enqueued since the counter was last read
+  int64_t init_launches = 0, body_launches = 0;
+
+  ~Ctx() { release(); }
+  void release_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+  }
+  void release_device() {
+    release_graph();
+    for (void* a : allocs) cudaFree(a);
+    allocs.clear();
+    L.clear();
+  }
+  void release() {
+    release_device();
+    if (st_host) cudaFreeHost(st_host);
+    st_host = nullptr;
+    if (s) cudaStreamDestroy(s);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    s = nullptr; ev_in = ev_out = t0 = t1 = nullptr;
+  }
+  template <class T>
+  int alloc(T** ptr, int64_t count) {
+    *ptr = nullptr;
+    if (count <= 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) return fail(AMGF_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(p);
+    *ptr = (T*)p;
+    return AMGF_OK;
+  }
+  template <class T>
+  int upload(T** ptr, const T* host, int64_t count) {
+    int st_ = alloc(ptr, count);
+    if (st_) return st_;
+    if (count > 0) CK(cudaMemcpy(*ptr, host, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
+    return AMGF_OK;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// launch helpers
+
+static int lanes_for(double avg_nnz) {
+  if (avg_nnz >= 48) return 32;
+  if (avg_nnz >= 20) return 16;
+  if (avg_nnz >= 9) return 8;
+  if (avg_nnz >= 4) return 4;
+  return 2;
+}
+
+static int grid_for(const Ctx& c, int64_t rows, int K) {
+  const int64_t need = (rows * K + TPB - 1) / TPB;
+  const int64_t cap = (int64_t)c.num_sms * 8;  // 8 resident blocks of 256 threads per SM
+  int64_t g = need < cap ? need : cap;
+  if (g > MAX_DOT_BLOCKS) g = MAX_DOT_BLOCKS;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <int MODE, bool DOT>
+static void launch_csr_k(int K, int grid, cudaStream_t s, const CsrArgs& a) {
+  switch (K) {
+    case 32: csr_kernel<32, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    case 16: csr_kernel<16, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    case 8: csr_kernel<8, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    case 4: csr_kernel<4, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    default: csr_kernel<2, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+  }
+}
+
+template <int MODE>
+static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nullptr, double* result = nullptr) {
+  a.rp = A.rp; a.ci = A.ci; a.v = A.v; a.nrows = A.nrows;
+  if (A.nrows == 0) return;
+  c.launches++;
+  const int grid = grid_for(c, A.nrows, A.K);
+  if (result) {
+    a.dotv = dotv; a.partial = c.partial; a.result = result; a.counter = c.counter;
+    launch_csr_k<MODE, true>(A.K, grid, c.s, a);
+  } else {
+    launch_csr_k<MODE, false>(A.K, grid, c.s, a);
+  }
+}
+
+static int vec_grid(const Ctx& c, int64_t n) {
+  int64_t g = (n + TPB - 1) / TPB;
+  const int64_t cap = (int64_t)c.num_sms * 8;
+  return (int)(g < 1 ? 1 : (g < cap ? g : cap));
+}
+
+// ---------------------------------------------------------------------------------------
+// V-cycle: out0 = B rhs0 (+ add0); optional dot(dotv, out0) -> *dotres
+
+static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const double* add0, const double* dotv,
+                           double* dotres) {
+  const int nlev = (int)c.L.size();
+  const int nu = c.o.nu < 1 ? 1 : c.o.nu;
+  auto rhs_of = [&](int l) -> const double* { return l == 0 ? rhs0 : c.L[l].rhs; };
+  for (int l = 0; l + 1 < nlev; ++l) {
+    DLevel& lv = c.L[l];
+    CsrArgs a{};
+    a.b = rhs_of(l); a.winv = lv.winv; a.y = lv.res; a.y2 = lv.x;
+    launch_csr<M_PRE>(c, lv.A, a);
+    for (int s = 1; s < nu; ++s) {
+      axpy_w_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.x);
+      c.launches++;
+      CsrArgs rr{};
+      rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
+      launch_csr<M_RESID>(c, lv.A, rr);
+    }
+    CsrArgs rs{};
+    rs.x = lv.res; rs.y = c.L[l + 1].rhs;
+    launch_csr<M_SPMV>(c, lv.R, rs);
+  }
+  // coarsest level: exact solve with the dense inverse
+  {
+    const int lc = nlev - 1;
+    const double* rc = rhs_of(lc);
+    double* oc = lc == 0 ? out0 : c.L[lc].out;
+    dense_gemv_kernel<<<1, TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, lc == 0 ? add0 : nullptr, oc,
+                                          lc == 0 ? dotv : nullptr, lc == 0 ? dotres : nullptr);
+    c.launches++;
+  }
+  for (int l = nlev - 2; l >= 0; --l) {
+    DLevel& lv = c.L[l];
+    CsrArgs pa{};
+    pa.x = c.L[l + 1].out; pa.y = lv.x;
+    launch_csr<M_SPMV_ADD>(c, lv.P, pa);
+    for (int s = 1; s < nu; ++s) {
+      CsrArgs rr{};
+      rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
+      launch_csr<M_RESID>(c, lv.A, rr);
+      axpy_w_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.x);
+      c.launches++;
+    }
+    CsrArgs po{};
+    po.x = lv.x; po.b = rhs_of(l); po.winv = lv.winv;
+    po.add = l == 0 ? add0 : nullptr;
+    po.y = l == 0 ? out0 : lv.out;
+    if (l == 0 && dotres) launch_csr<M_POST>(c, lv.A, po, dotv, dotres);
+    else launch_csr<M_POST>(c, lv.A, po);
+  }
+}
+
+// w (factor order, length nblk*nb) = A_w^{-1} v, v gathered from r at gidx (or given directly)
+static void enqueue_filter_solve(Ctx& c, const double* r, const double* vdirect) {
+  const int64_t nb = c.F.nb, nblk = c.F.nblk;
+  const size_t smem = 2 * nb * sizeof(double);
+  filter_fwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fG, c.fgidx, r, vdirect, c.F.nc, nb, nblk, c.fy);
+  const int64_t rows = nb * nblk;
+  int g = (int)((rows * 32 + TPB - 1) / TPB);
+  if (g > c.num_sms * 8) g = c.num_sms * 8;
+  filter_diag_kernel<<<g, TPB, 0, c.s>>>(c.fDinv, c.fy, c.fz, nb, nblk);
+  filter_bwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fGT, c.fz, nb, nblk, c.fw);
+  c.launches += 3;
+}
+
+// z = M r; optional dot(r, z) -> *dotres
+static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres) {
+  if (!c.o.filter) {  // M = B
+    enqueue_vcycle(c, r, z, nullptr, r, dotres);
+    return;
+  }
+  // y1 = B r
+  enqueue_vcycle(c, r, c.y1, nullptr, nullptr, nullptr);
+  // r1 = r - A y1
+  CsrArgs ra{};
+  ra.x = c.y1; ra.b = r; ra.y = c.r1;
+  launch_csr<M_RESID>(c, c.L[0].A, ra);
+  if (c.F.nc > 0) {
+    enqueue_filter_solve(c, c.r1, nullptr);
+    filter_scatter_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.fgidx, c.fw, c.y1, c.F.nc);  // y2 = y1 + P w
+    c.launches++;
+    CsrArgs sa{};
+    sa.rows = c.ftouch; sa.x = c.fw; sa.b = c.r1; sa.y = c.r1;                               // r2 = r1 - A P w
+    launch_csr<M_RESID>(c, c.fSc, sa);
+  }
+  // z = y2 + B r2
+  enqueue_vcycle(c, c.r1, z, c.y1, r, dotres);
+}
+
+// one PCG iteration (body of the while node)
+static void enqueue_pcg_body(Ctx& c, int use_cond) {
+  CsrArgs qa{};
+  qa.x = c.p; qa.y = c.q;
+  launch_csr<M_SPMV>(c, c.L[0].A, qa, c.p, &c.st->pq);
+  pcg_update_xr_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.p, c.q, c.x, c.r, c.n);
+  enqueue_apply(c, c.r, c.z, &c.st->rz_new);
+  pcg_update_p_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.z, c.p, c.n);
+  pcg_finalize_kernel<<<1, 1, 0, c.s>>>(c.st, c.cond, use_cond);
+  c.launches += 3;
+}
+
+static void enqueue_pcg_init(Ctx& c) {
+  CsrArgs ra{};
+  ra.x = c.x; ra.b = c.b; ra.y = c.r;
+  launch_csr<M_RESID>(c, c.L[0].A, ra);                 // r0 = b - A x0
+  enqueue_apply(c, c.r, c.z, &c.st->rz_new);             // z0 = M r0, rz_new = r0^T z0
+  pcg_init_kernel<<<1, 1, 0, c.s>>>(c.st, c.o.maxit, c.o.rtol);
+  copy_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.z, c.p);  // p0 = z0
+  c.launches += 2;
+}
+
+static int build_graph(Ctx& c) {
+  c.release_graph();
+  CK(cudaGraphCreate(&c.graph, 0));
+  // initial part, captured into its own graph and embedded as a child node
+  cudaGraph_t init_g = nullptr;
+  CK(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+  c.launches = 0;
+  enqueue_pcg_init(c);
+  c.init_launches = c.launches;
+  CK(cudaStreamEndCapture(c.s, &init_g));
+  cudaGraphNode_t init_node;
+  CK(cudaGraphAddChildGraphNode(&init_node, c.graph, nullptr, 0, init_g));
+  cudaGraphDestroy(init_g);
+  CK(cudaGraphConditionalHandleCreate(&c.cond, c.graph, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = c.cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t while_node;
+  CK(cudaGraphAddNode(&while_node, c.graph, &init_node, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(c.s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  c.launches = 0;
+  enqueue_pcg_body(c, 1);
+  c.body_launches = c.launches;
+  cudaGraph_t body_out = nullptr;
+  CK(cudaStreamEndCapture(c.s, &body_out));
+  CK(cudaGraphInstantiate(&c.gexec, c.graph, 0));
+  return AMGF_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// setup / upload
+
+static int upload_csr(Ctx& c, const HCSR& h, DCSR& d) {
+  d.nrows = h.nrows; d.ncols = h.ncols; d.nnz = h.nnz();
+  int st;
+  if ((st = c.upload(&d.rp, h.rp.data(), h.nrows + 1))) return st;
+  if ((st = c.upload(&d.ci, h.ci.data(), d.nnz))) return st;
+  if ((st = c.upload(&d.v, h.v.data(), d.nnz))) return st;
+  d.K = lanes_for(h.nrows ? (double)d.nnz / (double)h.nrows : 1.0);
+  return AMGF_OK;
+}
+
+static void fill_info(Ctx& c) {
+  amgf_info& in = c.info;
+  std::memset(&in, 0, sizeof in);
+  const int nlev = c.H.nlev();
+  in.n = c.n; in.m = c.m; in.nc = c.F.nc; in.nlevels = nlev;
+  double tot = 0.0;
+  for (int l = 0; l < nlev && l < 32; ++l) {
+    in.level_rows[l] = c.H.A[l].nrows;
+    in.level_nnz[l] = c.H.A[l].nnz();
+    tot += (double)c.H.A[l].nnz();
+    if (l + 1 < nlev) in.interp_nnz[l] = c.H.P[l].nnz();
+  }
+  in.op_complexity = tot / (double)c.H.A[0].nnz();
+  in.filter_block = c.F.nb;
+  in.filter_nblocks = c.F.nblk;
+}
+
+static int build_all(Ctx& c, const double* D) {
+  auto t_start = std::chrono::steady_clock::now();
+  std::string err;
+  amgf_csr K{c.Kh.nrows, c.Kh.ncols, c.Kh.nnz(), c.Kh.rp.data(), c.Kh.ci.data(), c.Kh.v.data()};
+  amgf_csr J{c.Jh.nrows, c.Jh.ncols, c.Jh.nnz(), c.Jh.rp.data(), c.Jh.ci.data(), c.Jh.v.data()};
+  HCSR S;
+  int st = assemble_S(&K, c.m > 0 ? &J : nullptr, D, S, err);
+  if (st) return fail(st, err);
+  st = build_hierarchy(S, c.o, c.H, err);
+  if (st) return fail(st, err);
+  if (c.o.filter) {
+    st = build_filter(S, c.m > 0 ? &J : nullptr, c.o, c.F, err);
+    if (st) return fail(st, err);
+  } else {
+    c.F = Filter();
+  }
+  S = HCSR();
+  fill_info(c);
+  c.info.t_setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  if (c.host_only) return AMGF_OK;
+  // ---- device upload
+  c.release_device();
+  const int nlev = c.H.nlev();
+  c.L.assign(nlev, DLevel());
+  for (int l = 0; l < nlev; ++l) {
+    DLevel& lv = c.L[l];
+    lv.n = c.H.A[l].nrows;
+    if ((st = upload_csr(c, c.H.A[l], lv.A))) return st;
+    if (l + 1 < nlev) {
+      if ((st = upload_csr(c, c.H.P[l], lv.P))) return st;
+      if ((st = upload_csr(c, c.H.R[l], lv.R))) return st;
+    }
+    std::vector<double> w(lv.n);
+    for (int64_t i = 0; i < lv.n; ++i) w[i] = 1.0 / c.H.l1[l][i];
+    if ((st = c.upload(&lv.winv, w.data(), lv.n))) return st;
+    if ((st = c.alloc(&lv.rhs, lv.n))) return st;
+    if ((st = c.alloc(&lv.x, lv.n))) return st;
+    if ((st = c.alloc(&lv.res, lv.n))) return st;
+    if ((st = c.alloc(&lv.out, lv.n))) return st;
+  }
+  c.nL = c.H.n_coarse;
+  if ((st = c.upload(&c.coarse_inv, c.H.coarse_inv.data(), c.nL * c.nL))) return st;
+  if (c.F.nc > 0) {
+    const int64_t tot = c.F.nb * c.F.nblk;
+    if ((st = c.upload(&c.fG, c.F.G.data(), tot * c.F.nb))) return st;
+    if ((st = c.upload(&c.fGT, c.F.GT.data(), tot * c.F.nb))) return st;
+    if ((st = c.upload(&c.fDinv, c.F.Dinv.data(), tot * c.F.nb))) return st;
+    if ((st = c.upload(&c.fgidx, c.F.gidx.data(), c.F.nc))) return st;
+    std::vector<int64_t> where(c.n, -1), fic(c.F.nc);
+    for (int64_t t = 0; t < c.F.nc; ++t) where[c.F.ic[t]] = t;
+    for (int64_t p = 0; p < c.F.nc; ++p) fic[p] = where[c.F.gidx[p]];
+    if ((st = c.upload(&c.ficidx, fic.data(), c.F.nc))) return st;
+    if ((st = c.upload(&c.ftouch, c.F.touch_rows.data(), (int64_t)c.F.touch_rows.size()))) return st;
+    if ((st = upload_csr(c, c.F.Sc, c.fSc))) return st;
+    if ((st = c.alloc(&c.fy, tot))) return st;
+    if ((st = c.alloc(&c.fz, tot))) return st;
+    if ((st = c.alloc(&c.fw, tot))) return st;
+    if ((st = c.alloc(&c.fv, tot))) return st;
+    // the filter sweeps need 2 * nb doubles of shared memory per CTA
+    const size_t smem = 2 * c.F.nb * sizeof(double);
+    if (smem > 200 * 1024) return fail(AMGF_ERR_INVALID_ARG, "filter block too large for shared memory");
+    CK(cudaFuncSetAttribute(filter_fwd_kernel<FILTER_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CK(cudaFuncSetAttribute(filter_bwd_kernel<FILTER_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  const int64_t n = c.n;
+  double** vecs[] = {&c.b, &c.x, &c.r, &c.z, &c.p, &c.q, &c.y1, &c.r1};
+  for (double** v : vecs) {
+    if ((st = c.alloc(v, n))) return st;
+    CK(cudaMemset(*v, 0, n * sizeof(double)));
+  }
+  if ((st = c.alloc(&c.partial, MAX_DOT_BLOCKS))) return st;
+  if ((st = c.alloc(&c.counter, 1))) return st;
+  CK(cudaMemset(c.counter, 0, sizeof(unsigned)));
+  if ((st = c.alloc(&c.scratch_scalar, 4))) return st;
+  if ((st = c.alloc(&c.st, 1))) return st;
+  CK(cudaMemset(c.st, 0, sizeof(PcgState)));
+  c.info.t_setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  amgf_info& in = c.info;
+  if (c.o.verbose) {
+    fprintf(stderr, "amgf: n=%lld m=%lld nc=%lld levels=%d opcx=%.3f filter nb=%lld nblk=%lld setup %.2fs\n",
+            (long long)c.n, (long long)c.m, (long long)c.F.nc, nlev, in.op_complexity, (long long)c.F.nb,
+            (long long)c.F.nblk, in.t_setup_s);
+  }
+  CK(cudaDeviceSynchronize());
+  return AMGF_OK;
+}
+
+static void copy_csr(const amgf_csr* a, HCSR& h) {
+  h.nrows = a->nrows; h.ncols = a->ncols;
+  h.rp.assign(a->row_ptr, a->row_ptr + a->nrows + 1);
+  h.ci.assign(a->col_idx, a->col_idx + a->nnz);
+  h.v.assign(a->val, a->val + a->nnz);
+}
+
+// join the caller's stream: library stream waits for it (begin) / caller waits for us (end)
+static int join_begin(Ctx& c, void* stream) {
+  CK(cudaEventRecord(c.ev_in, (cudaStream_t)stream));
+  CK(cudaStreamWaitEvent(c.s, c.ev_in, 0));
+  return AMGF_OK;
+}
+static int join_end(Ctx& c, void* stream) {
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(c.ev_out, c.s));
+  CK(cudaStreamWaitEvent((cudaStream_t)stream, c.ev_out, 0));
+  return AMGF_OK;
+}
+
+}  // namespace amgf
+
+using namespace amgf;
+
+struct amgf_ctx {
+  Ctx c;
+};
+
+extern "C" {
+
+int amgf_options_default(amgf_options* o) {
+  if (!o) return fail(AMGF_ERR_INVALID_ARG, "null options");
+  std::memset(o, 0, sizeof *o);
+  o->strength_theta = 0.8;
+  o->rtol = 1e-8;
+  o->max_levels = 25;
+  o->max_coarse = 128;
+  o->num_functions = 3;
+  o->nu = 1;
+  o->filter = 1;
+  o->contact_components = 0;
+  o->maxit = 5000;
+  o->use_graph = 1;
+  o->verbose = 0;
+  return AMGF_OK;
+}
+
+const char* amgf_last_error(void) { return g_last_error.c_str(); }
+
+static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, const amgf_options* o,
+                      amgf_handle* out, bool host_only) {
+  g_last_error.clear();
+  if (!out) return fail(AMGF_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  std::string err;
+  int st = validate_csr(K, "K", true, err);
+  if (st) return fail(st, err);
+  const bool has_j = J && J->nrows > 0;
+  if (has_j) {
+    st = validate_csr(J, "J", false, err);
+    if (st) return fail(st, err);
+    if (J->ncols != K->nrows) return fail(AMGF_ERR_INVALID_ARG, "J has the wrong number of columns");
+    if (!D) return fail(AMGF_ERR_INVALID_ARG, "null D");
+  }
+  amgf_options opt;
+  if (o) opt = *o; else amgf_options_default(&opt);
+  if (opt.nu < 1 || opt.max_levels < 1 || opt.max_coarse < 1 || opt.num_functions < 1 || !(opt.rtol > 0.0) ||
+      opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2)
+    return fail(AMGF_ERR_INVALID_ARG, "invalid options");
+  int ndev = 0;
+  if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");
+  std::unique_ptr<amgf_ctx> h(new (std::nothrow) amgf_ctx());
+  if (!h) return fail(AMGF_ERR_OOM, "host allocation");
+  Ctx& c = h->c;
+  c.o = opt;
+  c.host_only = host_only;
+  c.n = K->nrows;
+  c.m = has_j ? J->nrows : 0;
+  copy_csr(K, c.Kh);
+  if (has_j) copy_csr(J, c.Jh);
+  if (host_only) {
+    st = build_all(c, has_j ? D : nullptr);
+    if (st) return st;
+    *out = h.release();
+    return AMGF_OK;
+  }
+  CK(cudaGetDevice(&c.device));
+  CK(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+  CK(cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c.ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c.ev_out, cudaEventDisableTiming));
+  CK(cudaEventCreate(&c.t0));
+  CK(cudaEventCreate(&c.t1));
+  CK(cudaMallocHost(&c.st_host, sizeof(PcgState)));
+  st = build_all(c, has_j ? D : nullptr);
+  if (st) return st;
+  *out = h.release();
+  return AMGF_OK;
+}
+
+int amgf_setup(const amgf_csr* K, const amgf_csr* J, const double* D, const amgf_options* o, amgf_handle* out) {
+  return setup_impl(K, J, D, o, out, false);
+}
+
+int amgf_setup_host(const amgf_csr* K, const amgf_csr* J, const double* D, const amgf_options* o,
+                    amgf_handle* out) {
+  return setup_impl(K, J, D, o, out, true);
+}
+
+int amgf_update_D(amgf_handle h, const double* D) {
+  if (!h) return fail(AMGF_ERR_INVALID_ARG, "null handle");
+  if (h->c.m > 0 && !D) return fail(AMGF_ERR_INVALID_ARG, "null D");
+  if (!h->c.host_only) CK(cudaSetDevice(h->c.device));
+  return build_all(h->c, D);
+}
+
+int amgf_destroy(amgf_handle h) {
+  if (!h) return AMGF_OK;
+  if (!h->c.host_only) {
+    cudaSetDevice(h->c.device);
+    if (h->c.s) cudaStreamSynchronize(h->c.s);
+  }
+  delete h;
+  return AMGF_OK;
+}
+
+int amgf_apply(amgf_handle h, const double* r_dev, double* z_dev, void* stream) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !r_dev || !z_dev || r_dev == z_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  enqueue_apply(c, r_dev, z_dev, nullptr);
+  return join_end(c, stream);
+}
+
+int amgf_vcycle(amgf_handle h, const double* r_dev, double* x_dev, void* stream) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !r_dev || !x_dev || r_dev == x_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  enqueue_vcycle(c, r_dev, x_dev, nullptr, nullptr, nullptr);
+  return join_end(c, stream);
+}
+
+int amgf_matvec(amgf_handle h, const double* x_dev, double* y_dev, void* stream) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !x_dev || !y_dev || x_dev == y_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  CsrArgs a{};
+  a.x = x_dev; a.y = y_dev;
+  launch_csr<M_SPMV>(c, c.L[0].A, a);
+  return join_end(c, stream);
+}
+
+int amgf_filter_solve(amgf_handle h, const double* v_dev, double* w_dev, void* stream) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !v_dev || !w_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  if (c.F.nc == 0) return fail(AMGF_ERR_INVALID_ARG, "empty contact set");
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, nullptr, c.ficidx, v_dev, c.fv);
+  enqueue_filter_solve(c, nullptr, c.fv);
+  permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, c.ficidx, nullptr, c.fw, w_dev);
+  return join_end(c, stream);
+}
+
+static int solve_device(Ctx& c, amgf_stats* stats) {
+  // b and x already in c.b / c.x
+  CK(cudaEventRecord(c.t0, c.s));
+  if (c.o.use_graph) {
+    if (!c.gexec) {
+      int st = build_graph(c);
+      if (st) return st;
+    }
+    CK(cudaGraphLaunch(c.gexec, c.s));
+  } else {
+    c.launches = 0;
+    enqueue_pcg_init(c);
+    c.init_launches = c.launches;
+    for (int it = 0; it < c.o.maxit; ++it) {
+      CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(PcgState), cudaMemcpyDeviceToHost, c.s));
+      CK(cudaStreamSynchronize(c.s));
+      if (c.st_host->done) break;
+      c.launches = 0;
+      enqueue_pcg_body(c, 0);
+      c.body_launches = c.launches;
+    }
+  }
+  CK(cudaEventRecord(c.t1, c.s));
+  CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(PcgState), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  CK(cudaGetLastError());
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c.t0, c.t1));
+  const PcgState& s = *c.st_host;
+  if (stats) {
+    stats->iters = s.iter;
+    stats->converged = s.status == 0;
+    stats->status = s.status;
+    stats->nlevels = (int)c.L.size();
+    stats->rel_res_precond = s.relres;
+    stats->rz0 = s.rz0;
+    stats->t_solve_s = ms * 1e-3;
+    // kernels of the init part plus one body per executed loop trip (a body also runs once
+    // when the initial residual already meets the stop test)
+    const int64_t trips = s.iter > 0 ? s.iter : (c.o.use_graph ? 1 : 0);
+    stats->kernel_launches = c.init_launches + trips * c.body_launches;
+  }
+  if (s.status != 0) {
+    static const char* names[] = {"ok", "invalid", "non-finite PCG scalar", "not SPD", "breakdown (p^T A p <= 0 or r^T z < 0)",
+                                  "maximum iterations reached", "cuda", "oom"};
+    return fail(s.status, std::string("pcg: ") + names[s.status < 8 && s.status >= 0 ? s.status : 1]);
+  }
+  return AMGF_OK;
+}
+
+int amgf_pcg_solve(amgf_handle h, const double* b_dev, double* x_dev, amgf_stats* stats, void* stream) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !b_dev || !x_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  CK(cudaMemcpyAsync(c.b, b_dev, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+  CK(cudaMemcpyAsync(c.x, x_dev, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+  const int rs = solve_device(c, stats);
+  if (rs == AMGF_ERR_CUDA || rs == AMGF_ERR_OOM) return rs;
+  CK(cudaMemcpyAsync(x_dev, c.x, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+  st = join_end(c, stream);
+  return st ? st : rs;
+}
+
+int amgf_pcg_solve_host(amgf_handle h, const double* b_host, double* x_host, amgf_stats* stats) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !b_host || !x_host) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  CK(cudaSetDevice(c.device));
+  CK(cudaMemcpyAsync(c.b, b_host, c.n * sizeof(double), cudaMemcpyHostToDevice, c.s));
+  CK(cudaMemcpyAsync(c.x, x_host, c.n * sizeof(double), cudaMemcpyHostToDevice, c.s));
+  const int rs = solve_device(c, stats);
+  if (rs == AMGF_ERR_CUDA || rs == AMGF_ERR_OOM) return rs;
+  CK(cudaMemcpyAsync(x_host, c.x, c.n * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  return rs;
+}
+
+int amgf_get_info(amgf_handle h, amgf_info* info) {
+  if (!h || !info) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  *info = h->c.info;
+  return AMGF_OK;
+}
+
+int amgf_export_matrix(amgf_handle h, int which, int level, int64_t* nrows, int64_t* ncols, int64_t* nnz,
+                       int64_t* row_ptr, int32_t* col_idx, double* val) {
+  if (!h || !nrows || !ncols || !nnz) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  const Hierarchy& H = h->c.H;
+  const HCSR* a = nullptr;
+  if (which == 0 && level >= 0 && level < H.nlev()) a = &H.A[level];
+  else if (which == 1 && level >= 0 && level + 1 < H.nlev()) a = &H.P[level];
+  else if (which == 2 && level >= 0 && level + 1 < H.nlev()) a = &H.R[level];
+  if (!a) return fail(AMGF_ERR_INVALID_ARG, "no such matrix");
+  *nrows = a->nrows; *ncols = a->ncols; *nnz = a->nnz();
+  if (row_ptr) std::memcpy(row_ptr, a->rp.data(), (a->nrows + 1) * sizeof(int64_t));
+  if (col_idx) std::memcpy(col_idx, a->ci.data(), a->nnz() * sizeof(int32_t));
+  if (val) std::memcpy(val, a->v.data(), a->nnz() * sizeof(double));
+  return AMGF_OK;
+}
+
+int amgf_export_contact_set(amgf_handle h, int64_t* ic) {
+  if (!h || !ic) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  std::memcpy(ic, h->c.F.ic.data(), h->c.F.nc * sizeof(int64_t));
+  return AMGF_OK;
+}
+
+int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* stream, double* ms, double* bytes) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !ms || !bytes || reps < 1 || warmup < 0 || which < 0 || which > 1)
+    return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  DLevel& l0 = c.L[0];
+  const double nnz = (double)l0.A.nnz, n = (double)l0.n;
+  auto launch = [&]() {
+    if (which == 0) {
+      CsrArgs a{};
+      a.x = c.p; a.y = c.q;
+      launch_csr<M_SPMV>(c, l0.A, a);
+    } else {
+      CsrArgs a{};
+      a.x = c.p; a.b = c.r; a.winv = l0.winv; a.y = c.q;
+      launch_csr<M_POST>(c, l0.A, a);
+    }
+  };
+  for (int i = 0; i < warmup; ++i) launch();
+  CK(cudaEventRecord(c.t0, c.s));
+  for (int i = 0; i < reps; ++i) launch();
+  CK(cudaEventRecord(c.t1, c.s));
+  CK(cudaEventSynchronize(c.t1));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, c.t0, c.t1));
+  *ms = t / reps;
+  // values (8 B) + column indices (4 B) per nonzero, row pointers, and each vector read/written once
+  const double vec_bytes = which == 0 ? 2.0 * 8.0 * n : 4.0 * 8.0 * n;
+  *bytes = nnz * 12.0 + (n + 1) * 8.0 + vec_bytes;
+  return join_end(c, stream);
+}
+
+}  // extern "C"

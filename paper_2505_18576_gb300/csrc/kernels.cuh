@@ -1,0 +1,353 @@
+// CUDA kernels of the AMGF solve phase (sm_103a).
+//
+// Everything here is bandwidth- or latency-bound sparse/vector work:
+//   - csr_kernel<K, MODE, DOT>: one group of K lanes per row (K = 2..32), coalesced
+//     loads of the row's values and column indices, shuffle reduction.  The epilogue
+//     fuses what the V-cycle and PCG need around each A x:
+//       SPMV      y = A x
+//       SPMV_ADD  y += A x                         (prolongation x_l += P_l e_{l+1})
+//       RESID     y = b - A x                      (r1 = r - A y1, residual sweeps)
+//       PRE       x = W b ; y = b - A W b          (l1-Jacobi from zero + residual)
+//       POST      y = x + W (b - A x) [+ add]      (l1-Jacobi sweep; z = y2 + B r2)
+//     with W = diag(1 / l1), and optionally a deterministic dot product of the output
+//     with another vector (p^T A p, r^T z) finished by the last block to arrive.
+//   - dense_gemv: coarsest-level solve with the host-computed inverse.
+//   - filter_fwd / filter_bwd: block-tridiagonal LDL^T sweeps of A_w (Section 5.1),
+//     run by one thread-block cluster that keeps the running block vector in
+//     distributed shared memory; filter_diag applies the block pivots in parallel.
+//   - PCG scalar/vector kernels with device-resident scalars.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace amgf {
+
+constexpr int TPB = 256;          // threads per block of the row kernels
+constexpr int MAX_DOT_BLOCKS = 4096;
+
+enum : int { M_SPMV = 0, M_SPMV_ADD = 1, M_RESID = 2, M_PRE = 3, M_POST = 4 };
+
+struct CsrArgs {
+  const int64_t* __restrict__ rp;
+  const int32_t* __restrict__ ci;
+  const double* __restrict__ v;
+  int64_t nrows;
+  const int64_t* __restrict__ rows;  // optional row indirection (output row = rows[i])
+  const double* x;      // gathered vector (unused by PRE)
+  const double* b;      // right-hand side (RESID, PRE, POST)
+  const double* winv;   // 1 / l1 (PRE, POST)
+  const double* add;    // POST: optional vector added to the output
+  double* y;            // output
+  double* y2;           // PRE: x = W b
+  const double* dotv;   // DOT: partner vector of the output
+  double* partial;      // DOT: one partial per block
+  double* result;       // DOT: final scalar
+  unsigned* counter;    // DOT: arrival counter (zero between launches)
+};
+
+struct PcgState {
+  double rz;       // r_k^T z_k
+  double rz0;      // r_0^T z_0
+  double rz_new;   // written by the preconditioner's last kernel
+  double pq;       // p^T A p
+  double relres;   // sqrt(rz / rz0)
+  double rtol;
+  int iter;
+  int maxit;
+  int done;
+  int status;
+};
+
+__device__ __forceinline__ double warp_sum(double s) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
+// Deterministic grid reduction: block partial -> partial[blockIdx.x]; the last block to
+// arrive sums the partials in index order and writes *result.
+__device__ __forceinline__ void grid_dot_finish(double local, double* partial, double* result, unsigned* counter) {
+  __shared__ double red[TPB / 32];
+  __shared__ bool last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  local = warp_sum(local);
+  if (lane == 0) red[warp] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partial[blockIdx.x] = t;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(partial + i);
+  s = warp_sum(s);
+  __syncthreads();
+  if (lane == 0) red[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *result = t;
+    *counter = 0u;
+  }
+}
+
+template <int K, int MODE, bool DOT>
+__global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
+  static_assert(K >= 1 && K <= 32 && (K & (K - 1)) == 0, "K must be a power of two <= 32");
+  const int lane_w = threadIdx.x & 31;
+  const int sub = lane_w & (K - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * TPB + threadIdx.x) / K;
+  const int64_t warp_first = gid - (lane_w / K);
+  const int64_t stride = (int64_t)gridDim.x * (TPB / K);
+  double dacc = 0.0;
+  for (int64_t base = warp_first; base < a.nrows; base += stride) {
+    const int64_t i = base + lane_w / K;
+    const bool valid = i < a.nrows;
+    double s = 0.0;
+    if (valid) {
+      const int64_t k1 = a.rp[i + 1];
+      for (int64_t k = a.rp[i] + sub; k < k1; k += K) {
+        const int32_t j = a.ci[k];
+        double xv;
+        if (MODE == M_PRE) xv = a.winv[j] * a.b[j];
+        else xv = a.x[j];
+        s += a.v[k] * xv;
+      }
+    }
+#pragma unroll
+    for (int off = K / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, K);
+    if (valid && sub == 0) {
+      const int64_t o = a.rows ? a.rows[i] : i;
+      double out;
+      if (MODE == M_SPMV) out = s;
+      else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
+      else if (MODE == M_RESID) out = a.b[o] - s;
+      else if (MODE == M_PRE) { a.y2[o] = a.winv[o] * a.b[o]; out = a.b[o] - s; }
+      else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
+      a.y[o] = out;
+      if (DOT) dacc += a.dotv[o] * out;
+    }
+  }
+  if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
+}
+
+// x_i += W_i * res_i (extra pre-smoothing sweeps when nu > 1)
+__global__ void axpy_w_kernel(int64_t n, const double* __restrict__ winv, const double* __restrict__ res, double* x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += winv[i] * res[i];
+}
+
+// out = Ainv * r (+ add), Ainv dense n x n row-major; optional dot(dotv, out). One block.
+__global__ void __launch_bounds__(TPB) dense_gemv_kernel(int64_t n, const double* __restrict__ Ainv,
+                                                         const double* __restrict__ r, const double* add,
+                                                         double* out, const double* dotv, double* result) {
+  __shared__ double red[TPB / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double dacc = 0.0;
+  for (int64_t i = warp; i < n; i += nw) {
+    const double* row = Ainv + i * n;
+    double s = 0.0;
+    for (int64_t k = lane; k < n; k += 32) s += row[k] * r[k];
+    s = warp_sum(s);
+    if (add) s += add[i];
+    if (lane == 0) { out[i] = s; if (dotv) dacc += dotv[i] * s; }
+  }
+  if (result) {
+    dacc = warp_sum(dacc);
+    if (lane == 0) red[warp] = dacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[w];
+      *result = t;
+    }
+  }
+}
+
+// ---------------- filter: A_w^{-1} via block LDL^T (block-tridiagonal A_w) ----------------
+
+constexpr int FILTER_CS = 8;    // CTAs per cluster
+constexpr int FILTER_TPB = 512;
+
+// Forward sweep: y_0 = v_0, y_i = v_i - G_i y_{i-1}; v_p = r[gidx[p]] (0 on padding rows).
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(FILTER_TPB)
+filter_fwd_kernel(const double* __restrict__ G, const int64_t* __restrict__ gidx, const double* __restrict__ r,
+                  const double* __restrict__ vdirect, int64_t nc, int64_t nb, int64_t nblk, double* y) {
+  namespace cgp = cooperative_groups;
+  cgp::cluster_group cluster = cgp::this_cluster();
+  extern __shared__ double ybuf[];  // [2][nb]
+  const int rank = (int)cluster.block_rank();
+  const int64_t rpc = (nb + CS - 1) / CS;
+  const int64_t r0 = rank * rpc;
+  const int64_t r1 = r0 + rpc < nb ? r0 + rpc : nb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t i = 0; i < nblk; ++i) {
+    const int cur = (int)(i & 1);
+    const double* Gi = G + i * nb * nb;
+    const double* yprev = ybuf + (cur ^ 1) * nb;
+    for (int64_t rr = r0 + warp; rr < r1; rr += nw) {
+      const int64_t p = i * nb + rr;
+      double s = 0.0;
+      if (i > 0) {
+        const double* row = Gi + rr * nb;
+        for (int64_t k = lane; k < nb; k += 32) s += row[k] * yprev[k];
+      }
+      s = warp_sum(s);
+      double vin = 0.0;
+      if (p < nc) vin = vdirect ? vdirect[p] : r[gidx[p]];
+      const double val = vin - s;
+      if (lane < CS) {
+        double* dst = cluster.map_shared_rank(ybuf, lane);
+        dst[cur * nb + rr] = val;
+      }
+      if (lane == 0) y[p] = val;
+    }
+    cluster.sync();
+  }
+}
+
+// z_i = Dinv_i y_i for all blocks in parallel (one warp per row).
+__global__ void __launch_bounds__(TPB) filter_diag_kernel(const double* __restrict__ Dinv, const double* __restrict__ y,
+                                                          double* z, int64_t nb, int64_t nblk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nrow = nb * nblk;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t ws = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = w0; p < nrow; p += ws) {
+    const int64_t blk = p / nb, rr = p % nb;
+    const double* row = Dinv + blk * nb * nb + rr * nb;
+    const double* yb = y + blk * nb;
+    double s = 0.0;
+    for (int64_t k = lane; k < nb; k += 32) s += row[k] * yb[k];
+    s = warp_sum(s);
+    if (lane == 0) z[p] = s;
+  }
+}
+
+// Backward sweep: w_{N-1} = z_{N-1}, w_i = z_i - G_{i+1}^T w_{i+1}.
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(FILTER_TPB)
+filter_bwd_kernel(const double* __restrict__ GT, const double* __restrict__ z, int64_t nb, int64_t nblk, double* w) {
+  namespace cgp = cooperative_groups;
+  cgp::cluster_group cluster = cgp::this_cluster();
+  extern __shared__ double xbuf[];  // [2][nb]
+  const int rank = (int)cluster.block_rank();
+  const int64_t rpc = (nb + CS - 1) / CS;
+  const int64_t r0 = rank * rpc;
+  const int64_t r1 = r0 + rpc < nb ? r0 + rpc : nb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t t = 0; t < nblk; ++t) {
+    const int64_t i = nblk - 1 - t;
+    const int cur = (int)(t & 1);
+    const double* xnext = xbuf + (cur ^ 1) * nb;
+    const double* GTn = GT + (i + 1) * nb * nb;  // only read when i + 1 < nblk
+    for (int64_t rr = r0 + warp; rr < r1; rr += nw) {
+      const int64_t p = i * nb + rr;
+      double s = 0.0;
+      if (i + 1 < nblk) {
+        const double* row = GTn + rr * nb;
+        for (int64_t k = lane; k < nb; k += 32) s += row[k] * xnext[k];
+      }
+      s = warp_sum(s);
+      const double val = z[p] - s;
+      if (lane < CS) {
+        double* dst = cluster.map_shared_rank(xbuf, lane);
+        dst[cur * nb + rr] = val;
+      }
+      if (lane == 0) w[p] = val;
+    }
+    cluster.sync();
+  }
+}
+
+// y[gidx[p]] += w[p] for p < nc   (y2 = y1 + P w)
+__global__ void filter_scatter_kernel(const int64_t* __restrict__ gidx, const double* __restrict__ w, double* y, int64_t nc) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nc; p += (int64_t)gridDim.x * blockDim.x)
+    y[gidx[p]] += w[p];
+}
+
+// out[map[p]] = in[p] (map != null) or out[p] = in[map2[p]] -- permutations for the standalone filter solve
+__global__ void permute_kernel(int64_t n, const int64_t* __restrict__ scatter_to, const int64_t* __restrict__ gather_from,
+                               const double* __restrict__ in, double* out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (scatter_to) out[scatter_to[p]] = in[p];
+    else out[p] = in[gather_from[p]];
+  }
+}
+
+// ---------------- PCG ----------------
+
+// x += alpha p ; r -= alpha q with alpha = rz / pq (breakdown if pq <= 0)
+__global__ void pcg_update_xr_kernel(PcgState* st, const double* __restrict__ p, const double* __restrict__ q,
+                                     double* x, double* r, int64_t n) {
+  if (st->done) return;
+  const double pq = st->pq;
+  if (!(pq > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) { st->status = isfinite(pq) ? 4 : 2; st->done = 1; }
+    return;
+  }
+  const double alpha = st->rz / pq;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+// p = z + beta p with beta = rz_new / rz
+__global__ void pcg_update_p_kernel(const PcgState* st, const double* __restrict__ z, double* p, int64_t n) {
+  if (st->done) return;
+  const double beta = st->rz_new / st->rz;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// One thread: advance the iteration count and evaluate the stop test sqrt(rz/rz0) < rtol.
+__global__ void pcg_finalize_kernel(PcgState* st, cudaGraphConditionalHandle cond, int use_cond) {
+  if (!st->done) {
+    const double rzn = st->rz_new;
+    st->iter += 1;
+    if (!isfinite(rzn)) { st->status = 2; st->done = 1; }
+    else if (rzn < 0.0) { st->status = 4; st->done = 1; }
+    else {
+      st->relres = sqrt(rzn / st->rz0);
+      st->rz = rzn;
+      if (st->relres < st->rtol) { st->status = 0; st->done = 1; }
+      else if (st->iter >= st->maxit) { st->status = 5; st->done = 1; }
+    }
+  }
+  if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+}
+
+// After r0 = b - A x0 and z0 = M r0 (rz_new = r0^T z0): initialise the scalars.
+__global__ void pcg_init_kernel(PcgState* st, int maxit, double rtol) {
+  const double rz = st->rz_new;
+  st->rz = rz;
+  st->rz0 = rz;
+  st->iter = 0;
+  st->maxit = maxit;
+  st->rtol = rtol;
+  st->relres = 1.0;
+  st->pq = 0.0;
+  st->done = 0;
+  st->status = 5;
+  if (!isfinite(rz)) { st->status = 2; st->done = 1; }
+  else if (rz < 0.0) { st->status = 4; st->done = 1; }
+  else if (rz == 0.0) { st->status = 0; st->done = 1; st->relres = 0.0; }
+  else if (maxit <= 0) { st->done = 1; }
+}
+
+__global__ void copy_kernel(int64_t n, const double* __restrict__ a, double* b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = a[i];
+}
+
+}  // namespace amgf

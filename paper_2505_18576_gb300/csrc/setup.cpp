@@ -1,0 +1,653 @@
+// Host setup of the AMGF solver (C++17, OpenMP).
+//
+// B := AMG(A) (Section 5.1, Remark after Lemma "condition number estimate": classical
+// AMG with l1 smoothers; the paper uses hypre BoomerAMG).  The parameters and the
+// evaluation order of every floating-point sum are fixed so that the hierarchy is a
+// deterministic function of A:
+//   strength    j != i strong for i iff same unknown and |a_ij| >= theta * max_k |a_ik|
+//   coarsening  Ruge-Stueben first pass, largest measure first, ties to the smaller index,
+//               leftover points C if they have a strong influencer, else F
+//   interpolate direct interpolation with the sign split (Stueben), positive entries lumped
+//               into the diagonal when the row has no positive strong C neighbour
+//   Galerkin    R = P^T, A_c = R (A P), sums in ascending index order
+//   smoother    l1-Jacobi, l1_i = sum_j |a_ij|
+// A_w = P^T A P = A[I_c, I_c] (Section 5.1) is ordered by reverse Cuthill-McKee from a
+// pseudo-peripheral vertex (George & Liu) and factored as a block-tridiagonal LDL^T whose
+// block size is the bandwidth, giving an exact solve with dense block operations.
+#include "setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <queue>
+#include <utility>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace amgf {
+
+namespace {
+
+int nthreads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// Rows [0, n) split into `parts` contiguous ranges.
+std::vector<int64_t> split_rows(int64_t n, int parts) {
+  std::vector<int64_t> b(parts + 1);
+  for (int t = 0; t <= parts; ++t) b[t] = n * t / parts;
+  return b;
+}
+
+// Assemble per-range row pieces into one CSR (pieces are in row order).
+struct RowPieces {
+  std::vector<std::vector<int64_t>> len;   // per part: row lengths
+  std::vector<std::vector<int32_t>> ci;
+  std::vector<std::vector<double>> v;
+  explicit RowPieces(int parts) : len(parts), ci(parts), v(parts) {}
+  void gather(HCSR& out, int64_t nrows, int64_t ncols) {
+    out.nrows = nrows; out.ncols = ncols;
+    out.rp.assign(nrows + 1, 0);
+    int64_t r = 0;
+    for (auto& L : len)
+      for (int64_t x : L) { out.rp[r + 1] = out.rp[r] + x; ++r; }
+    out.ci.resize(out.rp[nrows]);
+    out.v.resize(out.rp[nrows]);
+    std::vector<int64_t> off(len.size() + 1, 0);
+    for (size_t t = 0; t < len.size(); ++t) off[t + 1] = off[t] + (int64_t)ci[t].size();
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < (int)len.size(); ++t) {
+      std::copy(ci[t].begin(), ci[t].end(), out.ci.begin() + off[t]);
+      std::copy(v[t].begin(), v[t].end(), out.v.begin() + off[t]);
+      std::vector<int32_t>().swap(ci[t]);
+      std::vector<double>().swap(v[t]);
+    }
+  }
+};
+
+HCSR transpose(const HCSR& a) {
+  HCSR t;
+  t.nrows = a.ncols; t.ncols = a.nrows;
+  t.rp.assign(t.nrows + 1, 0);
+  for (int64_t k = 0; k < a.nnz(); ++k) t.rp[a.ci[k] + 1]++;
+  for (int64_t i = 0; i < t.nrows; ++i) t.rp[i + 1] += t.rp[i];
+  t.ci.resize(a.nnz());
+  t.v.resize(a.nnz());
+  std::vector<int64_t> pos(t.rp.begin(), t.rp.end() - 1);
+  for (int64_t i = 0; i < a.nrows; ++i)
+    for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+      int64_t p = pos[a.ci[k]]++;
+      t.ci[p] = (int32_t)i;
+      t.v[p] = a.v[k];
+    }
+  return t;
+}
+
+// C = A B; entry (i, J) accumulates a_ij b_jJ over row i of A in ascending j.
+HCSR spgemm(const HCSR& a, const HCSR& b) {
+  const int parts = std::max(1, nthreads() * 4);
+  auto bounds = split_rows(a.nrows, parts);
+  RowPieces pc(parts);
+#pragma omp parallel
+  {
+    std::vector<double> acc(b.ncols, 0.0);
+    std::vector<int64_t> mark(b.ncols, -1);
+    std::vector<int32_t> cols;
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < parts; ++t) {
+      auto& L = pc.len[t];
+      auto& C = pc.ci[t];
+      auto& V = pc.v[t];
+      for (int64_t i = bounds[t]; i < bounds[t + 1]; ++i) {
+        cols.clear();
+        for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+          const int64_t j = a.ci[k];
+          const double aij = a.v[k];
+          for (int64_t kk = b.rp[j]; kk < b.rp[j + 1]; ++kk) {
+            const int32_t J = b.ci[kk];
+            if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; cols.push_back(J); }
+            acc[J] += aij * b.v[kk];
+          }
+        }
+        std::sort(cols.begin(), cols.end());
+        L.push_back((int64_t)cols.size());
+        for (int32_t J : cols) { C.push_back(J); V.push_back(acc[J]); }
+      }
+    }
+  }
+  HCSR c;
+  pc.gather(c, a.nrows, b.ncols);
+  return c;
+}
+
+// Strong influences S_i as a pattern (ascending, subset of row i of A).
+void strength_graph(const HCSR& A, const std::vector<int32_t>& func, double theta,
+                    std::vector<int64_t>& srp, std::vector<int32_t>& sci) {
+  const int64_t n = A.nrows;
+  std::vector<int64_t> cnt(n + 1, 0);
+  std::vector<double> thr(n, 0.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double mx = 0.0;
+    for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int32_t j = A.ci[k];
+      if (j == i || func[j] != func[i]) continue;
+      mx = std::max(mx, std::fabs(A.v[k]));
+    }
+    int64_t c = 0;
+    if (mx > 0.0) {
+      const double t = theta * mx;
+      thr[i] = t;
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int32_t j = A.ci[k];
+        if (j != i && func[j] == func[i] && std::fabs(A.v[k]) >= t) ++c;
+      }
+    }
+    cnt[i + 1] = c;
+  }
+  for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  srp = cnt;
+  sci.resize(srp[n]);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    if (srp[i + 1] == srp[i]) continue;
+    int64_t p = srp[i];
+    for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int32_t j = A.ci[k];
+      if (j != i && func[j] == func[i] && std::fabs(A.v[k]) >= thr[i]) sci[p++] = j;
+    }
+  }
+}
+
+// Ruge-Stueben first pass with a lazy max-heap keyed by (measure, -index).
+std::vector<int8_t> ruge_stueben(int64_t n, const std::vector<int64_t>& srp, const std::vector<int32_t>& sci) {
+  // dependents: transpose of the strength pattern
+  std::vector<int64_t> trp(n + 1, 0);
+  for (int32_t j : sci) trp[j + 1]++;
+  for (int64_t i = 0; i < n; ++i) trp[i + 1] += trp[i];
+  std::vector<int32_t> tci(sci.size());
+  {
+    std::vector<int64_t> pos(trp.begin(), trp.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t k = srp[i]; k < srp[i + 1]; ++k) tci[pos[sci[k]]++] = (int32_t)i;
+  }
+  enum : int8_t { UND = 0, FPT = 1, CPT = 2 };
+  std::vector<int8_t> state(n, UND);
+  std::vector<int64_t> lam(n);
+  using Key = std::pair<int64_t, int64_t>;  // (measure, -index): top = largest measure, smallest index
+  std::vector<Key> init(n);
+  for (int64_t i = 0; i < n; ++i) { lam[i] = trp[i + 1] - trp[i]; init[i] = Key(lam[i], -i); }
+  std::priority_queue<Key> heap(std::less<Key>(), std::move(init));
+  while (!heap.empty()) {
+    const Key top = heap.top();
+    heap.pop();
+    const int64_t i = -top.second;
+    if (state[i] != UND || lam[i] != top.first) continue;  // stale entry
+    if (top.first <= 0) break;
+    state[i] = CPT;
+    for (int64_t k = trp[i]; k < trp[i + 1]; ++k) {
+      const int32_t j = tci[k];
+      if (state[j] != UND) continue;
+      state[j] = FPT;
+      for (int64_t kk = srp[j]; kk < srp[j + 1]; ++kk) {
+        const int32_t q = sci[kk];
+        if (state[q] == UND) { lam[q] += 1; heap.push(Key(lam[q], -(int64_t)q)); }
+      }
+    }
+    for (int64_t k = srp[i]; k < srp[i + 1]; ++k) {
+      const int32_t q = sci[k];
+      if (state[q] == UND) { lam[q] -= 1; heap.push(Key(lam[q], -(int64_t)q)); }
+    }
+  }
+  std::vector<int8_t> cf(n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (state[i] == UND) state[i] = (srp[i + 1] > srp[i]) ? CPT : FPT;
+    cf[i] = state[i] == CPT ? 1 : 0;
+  }
+  return cf;
+}
+
+// Direct interpolation with the sign split.
+HCSR direct_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const std::vector<int32_t>& sci,
+                          const std::vector<int32_t>& func, const std::vector<int8_t>& cf, int64_t& nc) {
+  const int64_t n = A.nrows;
+  std::vector<int64_t> cidx(n, -1);
+  nc = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (cf[i]) cidx[i] = nc++;
+  const int parts = std::max(1, nthreads() * 4);
+  auto bounds = split_rows(n, parts);
+  RowPieces pc(parts);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < parts; ++t) {
+    auto& L = pc.len[t];
+    auto& C = pc.ci[t];
+    auto& V = pc.v[t];
+    for (int64_t i = bounds[t]; i < bounds[t + 1]; ++i) {
+      if (cf[i]) { L.push_back(1); C.push_back((int32_t)cidx[i]); V.push_back(1.0); continue; }
+      bool anyC = false;
+      for (int64_t k = srp[i]; k < srp[i + 1]; ++k) anyC |= cf[sci[k]] != 0;
+      if (!anyC) { L.push_back(0); continue; }
+      // walk row i of A and the (ascending) strong list together
+      double diag = 0.0, sn = 0.0, sp = 0.0, cn = 0.0, cp = 0.0;
+      int64_t s = srp[i];
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int32_t j = A.ci[k];
+        const double a = A.v[k];
+        if (j == i) { diag = a; continue; }
+        if (func[j] != func[i]) continue;
+        while (s < srp[i + 1] && sci[s] < j) ++s;
+        const bool strongC = s < srp[i + 1] && sci[s] == j && cf[j];
+        if (a < 0.0) { sn += a; if (strongC) cn += a; }
+        else { sp += a; if (strongC) cp += a; }
+      }
+      if (cp == 0.0) diag += sp;
+      const double alpha = cn != 0.0 ? sn / cn : 0.0;
+      const double beta = cp != 0.0 ? sp / cp : 0.0;
+      int64_t cnt = 0;
+      s = srp[i];
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int32_t j = A.ci[k];
+        if (j == i) continue;
+        while (s < srp[i + 1] && sci[s] < j) ++s;
+        if (!(s < srp[i + 1] && sci[s] == j && cf[j])) continue;
+        const double a = A.v[k];
+        const double w = a < 0.0 ? -(alpha * a) / diag : -(beta * a) / diag;
+        C.push_back((int32_t)cidx[j]);
+        V.push_back(w);
+        ++cnt;
+      }
+      L.push_back(cnt);
+    }
+  }
+  HCSR P;
+  pc.gather(P, n, nc);
+  return P;
+}
+
+// In-place dense Cholesky (row-major, lower); false on a non-positive pivot.
+bool cholesky(std::vector<double>& a, int64_t n) {
+  for (int64_t j = 0; j < n; ++j) {
+    double s = a[j * n + j];
+    for (int64_t k = 0; k < j; ++k) s -= a[j * n + k] * a[j * n + k];
+    if (!(s > 0.0)) return false;
+    const double d = std::sqrt(s);
+    a[j * n + j] = d;
+#pragma omp parallel for schedule(static) if (n > 256)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double t = a[i * n + j];
+      for (int64_t k = 0; k < j; ++k) t -= a[i * n + k] * a[j * n + k];
+      a[i * n + j] = t / d;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i + 1; j < n; ++j) a[i * n + j] = 0.0;
+  return true;
+}
+
+// Inverse of an SPD matrix from its Cholesky factor: columns solve L L^T x = e_k.
+bool spd_inverse(const std::vector<double>& a, int64_t n, std::vector<double>& inv) {
+  std::vector<double> L(a);
+  if (!cholesky(L, n)) return false;
+  inv.assign(n * n, 0.0);
+#pragma omp parallel for schedule(dynamic, 4) if (n > 64)
+  for (int64_t c = 0; c < n; ++c) {
+    std::vector<double> y(n, 0.0);
+    for (int64_t i = c; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int64_t k = c; k < i; ++k) s -= L[i * n + k] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int64_t k = i + 1; k < n; ++k) s -= L[k * n + i] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int64_t i = 0; i < n; ++i) inv[i * n + c] = y[i];
+  }
+  // exact symmetry
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i + 1; j < n; ++j) {
+      const double s = 0.5 * (inv[i * n + j] + inv[j * n + i]);
+      inv[i * n + j] = inv[j * n + i] = s;
+    }
+  return true;
+}
+
+// C = A * B (n x n, row-major), C = alpha * A * B + beta * C
+void gemm(int64_t n, const double* A, const double* B, double* C, double alpha, double beta) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    std::vector<double> row(n, 0.0);
+    for (int64_t k = 0; k < n; ++k) {
+      const double a = A[i * n + k];
+      if (a == 0.0) continue;
+      const double* b = B + k * n;
+      for (int64_t j = 0; j < n; ++j) row[j] += a * b[j];
+    }
+    for (int64_t j = 0; j < n; ++j) C[i * n + j] = alpha * row[j] + (beta == 0.0 ? 0.0 : beta * C[i * n + j]);
+  }
+}
+
+}  // namespace
+
+int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& err) {
+  char buf[256];
+  if (!a || a->nrows < 0 || a->ncols <= 0 || a->nnz < 0 || (a->nrows > 0 && (!a->row_ptr || !a->col_idx || !a->val))) {
+    snprintf(buf, sizeof buf, "%s: null or negative-size CSR", name); err = buf; return AMGF_ERR_INVALID_ARG;
+  }
+  if (square && a->nrows != a->ncols) { snprintf(buf, sizeof buf, "%s: not square", name); err = buf; return AMGF_ERR_INVALID_ARG; }
+  if (a->ncols > INT32_MAX) { snprintf(buf, sizeof buf, "%s: too many columns for int32 indices", name); err = buf; return AMGF_ERR_INVALID_ARG; }
+  if (a->nrows == 0) return AMGF_OK;
+  if (a->row_ptr[0] != 0 || a->row_ptr[a->nrows] != a->nnz) { snprintf(buf, sizeof buf, "%s: row_ptr[0] or row_ptr[n] wrong", name); err = buf; return AMGF_ERR_INVALID_ARG; }
+  int bad = 0, nonfinite = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad, nonfinite)
+  for (int64_t i = 0; i < a->nrows; ++i) {
+    if (a->row_ptr[i + 1] < a->row_ptr[i]) { bad |= 1; continue; }
+    for (int64_t k = a->row_ptr[i]; k < a->row_ptr[i + 1]; ++k) {
+      const int64_t c = a->col_idx[k];
+      if (c < 0 || c >= a->ncols || (k > a->row_ptr[i] && c <= a->col_idx[k - 1])) bad |= 1;
+      if (!std::isfinite(a->val[k])) nonfinite |= 1;
+    }
+  }
+  if (bad) { snprintf(buf, sizeof buf, "%s: row_ptr not monotone or column indices unsorted/out of range", name); err = buf; return AMGF_ERR_INVALID_ARG; }
+  if (nonfinite) { snprintf(buf, sizeof buf, "%s: non-finite value", name); err = buf; return AMGF_ERR_NONFINITE; }
+  return AMGF_OK;
+}
+
+int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, std::string& err) {
+  const int64_t n = K->nrows;
+  const int64_t m = J ? J->nrows : 0;
+  for (int64_t r = 0; r < m; ++r) {
+    if (!std::isfinite(D[r])) { err = "D has a non-finite entry"; return AMGF_ERR_NONFINITE; }
+    if (!(D[r] > 0.0)) { err = "D has a non-positive entry"; return AMGF_ERR_NOT_SPD; }
+  }
+  // column lists of J: for DOF a, the constraints r (ascending) with J_ra != 0
+  std::vector<int64_t> crp(n + 1, 0);
+  std::vector<int64_t> crow;
+  std::vector<double> cval;
+  if (m > 0) {
+    for (int64_t k = 0; k < J->nnz; ++k) crp[J->col_idx[k] + 1]++;
+    for (int64_t i = 0; i < n; ++i) crp[i + 1] += crp[i];
+    crow.resize(J->nnz);
+    cval.resize(J->nnz);
+    std::vector<int64_t> pos(crp.begin(), crp.end() - 1);
+    for (int64_t r = 0; r < m; ++r)
+      for (int64_t k = J->row_ptr[r]; k < J->row_ptr[r + 1]; ++k) {
+        const int64_t p = pos[J->col_idx[k]]++;
+        crow[p] = r;
+        cval[p] = J->val[k];
+      }
+  }
+  const int parts = std::max(1, nthreads() * 4);
+  auto bounds = split_rows(n, parts);
+  RowPieces pc(parts);
+#pragma omp parallel
+  {
+    std::vector<double> acc(n, 0.0);
+    std::vector<int64_t> mark(n, -1);
+    std::vector<int32_t> cols;
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < parts; ++t) {
+      for (int64_t a = bounds[t]; a < bounds[t + 1]; ++a) {
+        cols.clear();
+        for (int64_t k = crp[a]; k < crp[a + 1]; ++k) {
+          const int64_t r = crow[k];
+          const double jra = cval[k];
+          for (int64_t kk = J->row_ptr[r]; kk < J->row_ptr[r + 1]; ++kk) {
+            const int32_t b = J->col_idx[kk];
+            const double djrb = D[r] * J->val[kk];
+            if (mark[b] != a) { mark[b] = a; acc[b] = 0.0; cols.push_back(b); }
+            acc[b] += jra * djrb;
+          }
+        }
+        std::sort(cols.begin(), cols.end());
+        // merge with row a of K (K value first, contact sum added to it)
+        int64_t p = K->row_ptr[a], pe = K->row_ptr[a + 1];
+        size_t q = 0;
+        int64_t cnt = 0;
+        while (p < pe || q < cols.size()) {
+          if (q >= cols.size() || (p < pe && K->col_idx[p] < cols[q])) {
+            pc.ci[t].push_back(K->col_idx[p]); pc.v[t].push_back(K->val[p]); ++p;
+          } else if (p >= pe || cols[q] < K->col_idx[p]) {
+            pc.ci[t].push_back(cols[q]); pc.v[t].push_back(acc[cols[q]]); ++q;
+          } else {
+            pc.ci[t].push_back(K->col_idx[p]); pc.v[t].push_back(K->val[p] + acc[cols[q]]); ++p; ++q;
+          }
+          ++cnt;
+        }
+        pc.len[t].push_back(cnt);
+      }
+    }
+  }
+  pc.gather(S, n, n);
+  return AMGF_OK;
+}
+
+int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::string& err) {
+  H = Hierarchy();
+  H.A.push_back(S);
+  H.func.emplace_back(S.nrows);
+  for (int64_t i = 0; i < S.nrows; ++i) H.func[0][i] = o.num_functions > 1 ? (int32_t)(i % o.num_functions) : 0;
+  int l = 0;
+  for (;;) {
+    const HCSR& A = H.A[l];
+    const int64_t n = A.nrows;
+    std::vector<double> l1(n);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) s += std::fabs(A.v[k]);
+      l1[i] = s;
+    }
+    H.l1.push_back(std::move(l1));
+    if (n <= o.max_coarse || l + 1 >= o.max_levels || l + 1 >= 32) break;
+    std::vector<int64_t> srp;
+    std::vector<int32_t> sci;
+    strength_graph(A, H.func[l], o.strength_theta, srp, sci);
+    std::vector<int8_t> cf = ruge_stueben(n, srp, sci);
+    int64_t nc = 0;
+    HCSR P = direct_interpolation(A, srp, sci, H.func[l], cf, nc);
+    if (nc == 0 || nc == n) break;  // coarsening stalled: this level is the coarsest
+    HCSR R = transpose(P);
+    HCSR AP = spgemm(A, P);
+    HCSR Ac = spgemm(R, AP);
+    std::vector<int32_t> fc;
+    fc.reserve(nc);
+    for (int64_t i = 0; i < n; ++i)
+      if (cf[i]) fc.push_back(H.func[l][i]);
+    H.P.push_back(std::move(P));
+    H.R.push_back(std::move(R));
+    H.A.push_back(std::move(Ac));
+    H.func.push_back(std::move(fc));
+    ++l;
+  }
+  const HCSR& AL = H.A.back();
+  const int64_t nL = AL.nrows;
+  if (nL > 8192) { err = "coarsest level too large for a dense solve"; return AMGF_ERR_INVALID_ARG; }
+  std::vector<double> dense(nL * nL, 0.0);
+  for (int64_t i = 0; i < nL; ++i)
+    for (int64_t k = AL.rp[i]; k < AL.rp[i + 1]; ++k) dense[i * nL + AL.ci[k]] = AL.v[k];
+  if (!spd_inverse(dense, nL, H.coarse_inv)) { err = "coarsest matrix is not SPD"; return AMGF_ERR_NOT_SPD; }
+  H.n_coarse = nL;
+  return AMGF_OK;
+}
+
+int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter& F, std::string& err) {
+  F = Filter();
+  const int64_t n = S.nrows;
+  std::vector<char> in(n, 0);
+  if (o.contact_components == 2) {
+    std::fill(in.begin(), in.end(), 1);
+  } else if (J && J->nrows > 0) {
+    const int64_t nf = std::max(1, o.num_functions);
+    for (int64_t k = 0; k < J->nnz; ++k) {
+      if (J->val[k] == 0.0) continue;
+      const int64_t c = J->col_idx[k];
+      if (o.contact_components == 1) {
+        const int64_t node = c / nf;
+        for (int64_t d = 0; d < nf; ++d)
+          if (node * nf + d < n) in[node * nf + d] = 1;
+      } else {
+        in[c] = 1;
+      }
+    }
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (in[i]) F.ic.push_back(i);
+  F.nc = (int64_t)F.ic.size();
+  if (F.nc == 0) return AMGF_OK;
+  const int64_t nc = F.nc;
+  std::vector<int64_t> where(n, -1);
+  for (int64_t t = 0; t < nc; ++t) where[F.ic[t]] = t;
+  // adjacency of A_w (I_c numbering)
+  HCSR Aw;
+  Aw.nrows = Aw.ncols = nc;
+  Aw.rp.assign(nc + 1, 0);
+  for (int64_t t = 0; t < nc; ++t) {
+    const int64_t i = F.ic[t];
+    for (int64_t k = S.rp[i]; k < S.rp[i + 1]; ++k) {
+      const int64_t p = where[S.ci[k]];
+      if (p >= 0) { Aw.ci.push_back((int32_t)p); Aw.v.push_back(S.v[k]); }
+    }
+    Aw.rp[t + 1] = (int64_t)Aw.ci.size();
+  }
+  // reverse Cuthill-McKee from a pseudo-peripheral vertex of each component
+  std::vector<int64_t> deg(nc);
+  for (int64_t t = 0; t < nc; ++t) deg[t] = Aw.rp[t + 1] - Aw.rp[t];
+  std::vector<char> seen(nc, 0);
+  std::vector<int64_t> order;
+  order.reserve(nc);
+  std::vector<int64_t> lvl(nc, -1);
+  auto bfs_levels = [&](int64_t root, std::vector<int64_t>& comp) {  // returns eccentricity
+    comp.clear();
+    comp.push_back(root);
+    lvl[root] = 0;
+    int64_t ecc = 0;
+    for (size_t h = 0; h < comp.size(); ++h) {
+      const int64_t u = comp[h];
+      for (int64_t k = Aw.rp[u]; k < Aw.rp[u + 1]; ++k) {
+        const int64_t v = Aw.ci[k];
+        if (lvl[v] < 0) { lvl[v] = lvl[u] + 1; ecc = std::max(ecc, lvl[v]); comp.push_back(v); }
+      }
+    }
+    return ecc;
+  };
+  std::vector<int64_t> comp;
+  for (int64_t s0 = 0; s0 < nc; ++s0) {
+    if (seen[s0]) continue;
+    // component of s0; start from its minimum-degree vertex
+    bfs_levels(s0, comp);
+    int64_t root = s0;
+    for (int64_t v : comp) if (deg[v] < deg[root] || (deg[v] == deg[root] && v < root)) root = v;
+    for (int64_t v : comp) lvl[v] = -1;
+    int64_t ecc = bfs_levels(root, comp);
+    for (int it = 0; it < 16; ++it) {
+      int64_t best = -1;
+      for (int64_t v : comp)
+        if (lvl[v] == ecc && (best < 0 || deg[v] < deg[best] || (deg[v] == deg[best] && v < best))) best = v;
+      for (int64_t v : comp) lvl[v] = -1;
+      const int64_t e2 = bfs_levels(best, comp);
+      if (e2 > ecc) { root = best; ecc = e2; continue; }
+      for (int64_t v : comp) lvl[v] = -1;
+      bfs_levels(root, comp);
+      break;
+    }
+    for (int64_t v : comp) lvl[v] = -1;
+    // Cuthill-McKee from root: neighbours by increasing degree
+    const size_t base = order.size();
+    order.push_back(root);
+    seen[root] = 1;
+    std::vector<std::pair<int64_t, int64_t>> nb;
+    for (size_t h = base; h < order.size(); ++h) {
+      const int64_t u = order[h];
+      nb.clear();
+      for (int64_t k = Aw.rp[u]; k < Aw.rp[u + 1]; ++k) {
+        const int64_t v = Aw.ci[k];
+        if (!seen[v]) { seen[v] = 1; nb.emplace_back(deg[v], v); }
+      }
+      std::sort(nb.begin(), nb.end());
+      for (auto& e : nb) order.push_back(e.second);
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  std::vector<int64_t> pos(nc);
+  for (int64_t p = 0; p < nc; ++p) pos[order[p]] = p;
+  int64_t bw = 0;
+  for (int64_t t = 0; t < nc; ++t)
+    for (int64_t k = Aw.rp[t]; k < Aw.rp[t + 1]; ++k) { const int64_t d = pos[t] - pos[Aw.ci[k]]; bw = std::max<int64_t>(bw, d < 0 ? -d : d); }
+  const int64_t nb = std::max<int64_t>(bw, 1);
+  const int64_t nblk = (nc + nb - 1) / nb;
+  F.nb = nb;
+  F.nblk = nblk;
+  F.gidx.resize(nc);
+  for (int64_t p = 0; p < nc; ++p) F.gidx[p] = F.ic[order[p]];
+  // dense diagonal and sub-diagonal blocks of the permuted A_w (padding rows = identity)
+  const int64_t bsz = nb * nb;
+  std::vector<double> Ad(nblk * bsz, 0.0), As(nblk * bsz, 0.0);  // As[i] = A_{i,i-1}
+  for (int64_t t = 0; t < nc; ++t) {
+    const int64_t pi = pos[t], bi = pi / nb, ri = pi % nb;
+    for (int64_t k = Aw.rp[t]; k < Aw.rp[t + 1]; ++k) {
+      const int64_t pj = pos[Aw.ci[k]], bj = pj / nb, rj = pj % nb;
+      if (bj == bi) Ad[bi * bsz + ri * nb + rj] = Aw.v[k];
+      else if (bj == bi - 1) As[bi * bsz + ri * nb + rj] = Aw.v[k];
+      else if (bj != bi + 1) { err = "filter ordering is not block tridiagonal"; return AMGF_ERR_INVALID_ARG; }
+    }
+  }
+  for (int64_t p = nc; p < nblk * nb; ++p) Ad[(p / nb) * bsz + (p % nb) * nb + (p % nb)] = 1.0;
+  // block LDL^T: D_0 = A_00; G_i = A_{i,i-1} D_{i-1}^{-1}; D_i = A_ii - G_i A_{i-1,i}
+  F.Dinv.assign(nblk * bsz, 0.0);
+  F.G.assign(nblk * bsz, 0.0);
+  F.GT.assign(nblk * bsz, 0.0);
+  std::vector<double> Dcur(Ad.begin(), Ad.begin() + bsz), tmp(bsz), AsT(bsz);
+  for (int64_t i = 0; i < nblk; ++i) {
+    if (i > 0) {
+      Dcur.assign(Ad.begin() + i * bsz, Ad.begin() + (i + 1) * bsz);
+      double* Gi = F.G.data() + i * bsz;
+      gemm(nb, As.data() + i * bsz, F.Dinv.data() + (i - 1) * bsz, Gi, 1.0, 0.0);
+      for (int64_t r = 0; r < nb; ++r)
+        for (int64_t c = 0; c < nb; ++c) AsT[r * nb + c] = As[i * bsz + c * nb + r];
+      gemm(nb, Gi, AsT.data(), Dcur.data(), -1.0, 1.0);
+      for (int64_t r = 0; r < nb; ++r)
+        for (int64_t c = r + 1; c < nb; ++c) {
+          const double s = 0.5 * (Dcur[r * nb + c] + Dcur[c * nb + r]);
+          Dcur[r * nb + c] = Dcur[c * nb + r] = s;
+        }
+      for (int64_t r = 0; r < nb; ++r)
+        for (int64_t c = 0; c < nb; ++c) F.GT[i * bsz + r * nb + c] = Gi[c * nb + r];
+    }
+    std::vector<double> inv;
+    if (!spd_inverse(Dcur, nb, inv)) { err = "filter matrix A_w is not SPD"; return AMGF_ERR_NOT_SPD; }
+    std::copy(inv.begin(), inv.end(), F.Dinv.begin() + i * bsz);
+  }
+  // A[:, I_c] on the rows that touch I_c, columns as factor positions
+  std::vector<int64_t> rowcnt(n, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0;
+    for (int64_t k = S.rp[i]; k < S.rp[i + 1]; ++k) c += where[S.ci[k]] >= 0;
+    rowcnt[i] = c;
+  }
+  F.Sc.rp.push_back(0);
+  for (int64_t i = 0; i < n; ++i) {
+    if (!rowcnt[i]) continue;
+    F.touch_rows.push_back(i);
+    for (int64_t k = S.rp[i]; k < S.rp[i + 1]; ++k) {
+      const int64_t t = where[S.ci[k]];
+      if (t >= 0) { F.Sc.ci.push_back((int32_t)pos[t]); F.Sc.v.push_back(S.v[k]); }
+    }
+    F.Sc.rp.push_back((int64_t)F.Sc.ci.size());
+  }
+  F.Sc.nrows = (int64_t)F.touch_rows.size();
+  F.Sc.ncols = nc;
+  return AMGF_OK;
+}
+
+}  // namespace amgf

@@ -1,0 +1,59 @@
+// Host-side setup of the AMGF solver: assembly of A = K + J^T D J, classical AMG
+// hierarchy, contact set I_c and the block-tridiagonal factor of A_w = P^T A P.
+// Internal to the library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/amgf.h"
+
+namespace amgf {
+
+struct HCSR {
+  int64_t nrows = 0, ncols = 0;
+  std::vector<int64_t> rp;   // nrows + 1
+  std::vector<int32_t> ci;
+  std::vector<double> v;
+  int64_t nnz() const { return rp.empty() ? 0 : rp.back(); }
+};
+
+struct Hierarchy {
+  std::vector<HCSR> A;                    // A[0] = S, A[l+1] = R_l A_l P_l
+  std::vector<HCSR> P, R;                 // P[l]: n_l x n_{l+1}, R[l] = P[l]^T
+  std::vector<std::vector<double>> l1;    // l1_i = sum_j |a_ij|
+  std::vector<std::vector<int32_t>> func; // unknown (displacement component) of each row
+  std::vector<double> coarse_inv;         // dense inverse of the coarsest A (row-major)
+  int64_t n_coarse = 0;
+  int nlev() const { return (int)A.size(); }
+};
+
+struct Filter {
+  int64_t nc = 0;                 // |I_c|
+  std::vector<int64_t> ic;        // I_c, ascending DOF indices
+  std::vector<int64_t> gidx;      // factor position p -> DOF index (p < nc)
+  int64_t nb = 0, nblk = 0;       // block size, number of diagonal blocks (nblk*nb >= nc)
+  std::vector<double> Dinv;       // nblk blocks nb x nb: inverse of the block pivots D_i
+  std::vector<double> G;          // nblk blocks: G_i = A_{i,i-1} D_{i-1}^{-1} (G_0 = 0)
+  std::vector<double> GT;         // transposes of G_i
+  // A[:, I_c] restricted to rows that touch I_c; columns are factor positions p
+  std::vector<int64_t> touch_rows;
+  HCSR Sc;
+};
+
+// Input validation; returns an amgf_status.
+int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& err);
+
+// A = K + J^T D J.  Entry (a, b) of J^T D J sums J_ra (D_r J_rb) over ascending r and is
+// added to K_ab after it.
+int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, std::string& err);
+
+// B := AMG(A): strength, Ruge-Stueben first pass, direct interpolation, Galerkin, l1 sums,
+// dense inverse of the coarsest level.
+int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::string& err);
+
+// I_c, A_w = A[I_c, I_c], reverse Cuthill-McKee order, block-tridiagonal LDL^T factor.
+int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter& F, std::string& err);
+
+}  // namespace amgf

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances (FP64 on both sides, different summation orders):
+  - A x: per row, |y_gpu - y_orc| <= 2 * gamma_k * (|A| |x|)_i with gamma_k = k eps / (1 - k eps),
+    k = nonzeros of the row (forward error bound of a dot product, both sides).
+  - V-cycle, AMGF apply: ||z_gpu - z_orc|| <= 1e-12 ||z_orc||.
+  - PCG: iteration counts equal within +-1 at rtol 1e-8; solutions within 1e-8 relative.
+The hierarchy itself is bit-identical (tests/test_library_host.py), so every difference
+comes from summation order in the kernels.
+"""
+import numpy as np
+import pytest
+
+import contactgen as cg
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def amgf():
+    import paper_2505_18576_gb300 as m
+    m.load_library()
+    return m
+
+
+def _pair(p, **opts):
+    import paper_2505_18576_gb300 as m
+    return oracle.Oracle(p.K, p.J, p.D, **opts), m.Solver(p.K, p.J, p.D, **opts)
+
+
+CASES = {
+    "tiny": dict(nx=8, ny=8, nz=4, d_lo=-2, d_hi=4),
+    "ragged": dict(nx=5, ny=3, nz=2, d_lo=-2, d_hi=8),
+    "n16": dict(nx=16, ny=12, nz=7, d_lo=-2, d_hi=8),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    p = cg.make_problem(None, seed=1, **CASES[request.param])
+    o, s = _pair(p)
+    yield request.param, p, o, s
+    s.close()
+
+
+def test_matvec_rowwise_error_bound(case):
+    name, p, o, s = case
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(p.n)
+    y = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.matvec(dev(x), y)
+    yg = host(y)
+    yo = o.S_apply(x)
+    S = o.S()
+    absAx = abs(S) @ np.abs(x)
+    k = np.diff(S.indptr)
+    gam = k * EPS / (1 - k * EPS)
+    assert np.all(np.abs(yg - yo) <= 2 * gam * absAx + 1e-300)
+
+
+def test_vcycle_parity(case):
+    name, p, o, s = case
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(p.n)
+    x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(r), x)
+    xo = o.vcycle(r)
+    assert np.linalg.norm(host(x) - xo) <= 1e-12 * np.linalg.norm(xo)
+
+
+def test_filter_solve_parity(case):
+    name, p, o, s = case
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal(o.nc)
+    w = torch.empty(o.nc, dtype=torch.float64, device="cuda")
+    s.filter_solve(dev(v), w)
+    wo = o.filter_solve(v)
+    assert np.linalg.norm(host(w) - wo) <= 1e-12 * np.linalg.norm(wo)
+
+
+def test_apply_parity(case):
+    name, p, o, s = case
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(p.n)
+    z = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.apply(dev(r), z)
+    zo = o.apply(r)
+    assert np.linalg.norm(host(z) - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+def test_pcg_parity(case):
+    name, p, o, s = case
+    xo, ko, sto, *_ = o.pcg(p.b, tol=1e-8)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(dev(p.b), x)
+    assert sto == 0 and st.status == 0 and st.converged == 1
+    assert abs(st.iters - ko) <= 1
+    assert np.linalg.norm(host(x) - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+def test_pcg_deterministic_and_graph_equals_stream(case):
+    import paper_2505_18576_gb300 as m
+    name, p, o, s = case
+    x1 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    s1 = s.pcg_solve(dev(p.b), x1)
+    s2 = s.pcg_solve(dev(p.b), x2)
+    assert s1.iters == s2.iters and torch.equal(x1, x2)
+    s_ng = m.Solver(p.K, p.J, p.D, use_graph=0)
+    x3 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    s3 = s_ng.pcg_solve(dev(p.b), x3)
+    assert s3.iters == s1.iters and torch.equal(x1, x3)
+    s_ng.close()
+
+
+def test_host_buffers_solve_equals_device(case):
+    name, p, o, s = case
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    s.pcg_solve(dev(p.b), x)
+    xh = np.zeros(p.n)
+    st = s.pcg_solve_host(np.ascontiguousarray(p.b), xh)
+    assert st.status == 0 and np.array_equal(xh, host(x))
+
+
+# ---------------------------------------------------------------- special cases
+
+
+def test_amg_only_mode(tiny):
+    o, s = _pair(tiny, filter=0)
+    r = np.random.default_rng(4).standard_normal(tiny.n)
+    z = torch.empty(tiny.n, dtype=torch.float64, device="cuda")
+    s.apply(dev(r), z)
+    zo = o.apply(r)
+    assert np.linalg.norm(host(z) - zo) <= 1e-12 * np.linalg.norm(zo)
+    xo, ko, *_ = o.pcg(tiny.b)
+    x = torch.zeros(tiny.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(dev(tiny.b), x)
+    assert abs(st.iters - ko) <= 1
+
+
+def test_P_identity_exact_inverse(tiny):
+    o, s = _pair(tiny, contact_components=2)
+    r = np.random.default_rng(5).standard_normal(tiny.n)
+    z = torch.empty(tiny.n, dtype=torch.float64, device="cuda")
+    s.apply(dev(r), z)
+    ref = np.linalg.solve(o.S().toarray(), r)
+    assert np.linalg.norm(host(z) - ref) <= 1e-9 * np.linalg.norm(ref)
+    x = torch.zeros(tiny.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(dev(r), x)
+    assert st.iters == 1
+
+
+def test_no_contact_two_B_minus_BAB(tiny):
+    import paper_2505_18576_gb300 as m
+    o = oracle.Oracle(tiny.K)
+    s = m.Solver(tiny.K)
+    assert s.nc == 0
+    r = np.random.default_rng(6).standard_normal(tiny.n)
+    z = torch.empty(tiny.n, dtype=torch.float64, device="cuda")
+    s.apply(dev(r), z)
+    zo = o.apply(r)
+    assert np.linalg.norm(host(z) - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+def test_zero_rhs_maxit_and_warm_start(tiny):
+    import paper_2505_18576_gb300 as m
+    o, s = _pair(tiny)
+    x = torch.zeros(tiny.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(torch.zeros(tiny.n, dtype=torch.float64, device="cuda"), x)
+    assert st.status == 0 and st.iters == 0 and not torch.any(x)
+    s3 = m.Solver(tiny.K, tiny.J, tiny.D, maxit=3)
+    x = torch.zeros(tiny.n, dtype=torch.float64, device="cuda")
+    st = s3.pcg_solve(dev(tiny.b), x, check=False)
+    assert st.status == 5 and st.iters == 3 and st.rc == 5
+    xo, *_ = o.pcg(tiny.b, tol=1e-12)
+    x0 = xo + 1e-3 * np.random.default_rng(7).standard_normal(tiny.n)
+    xw = dev(x0)
+    st = s.pcg_solve(dev(tiny.b), xw)
+    xr, kr, *_ = o.pcg(tiny.b, x0=x0)
+    assert abs(st.iters - kr) <= 1
+    assert np.linalg.norm(host(xw) - xr) <= 1e-8 * np.linalg.norm(xr)
+
+
+def test_update_D_matches_fresh_oracle(tiny):
+    import paper_2505_18576_gb300 as m
+    s = m.Solver(tiny.K, tiny.J, tiny.D)
+    D2, b2 = cg.draw_D_b(99, tiny.m, tiny.n, -2.0, 10.0)
+    s.update_D(D2)
+    o = oracle.Oracle(tiny.K, tiny.J, D2)
+    r = np.random.default_rng(8).standard_normal(tiny.n)
+    z = torch.empty(tiny.n, dtype=torch.float64, device="cuda")
+    s.apply(dev(r), z)
+    zo = o.apply(r)
+    assert np.linalg.norm(host(z) - zo) <= 1e-12 * np.linalg.norm(zo)
+
+
+def test_invalid_device_arguments(tiny):
+    import paper_2505_18576_gb300 as m
+    s = m.Solver(tiny.K, tiny.J, tiny.D)
+    with pytest.raises(m.AmgfError):
+        s.apply(torch.zeros(tiny.n - 1, dtype=torch.float64, device="cuda"),
+                torch.zeros(tiny.n, dtype=torch.float64, device="cuda"))
+    with pytest.raises(m.AmgfError):
+        s.apply(torch.zeros(tiny.n, dtype=torch.float32, device="cuda"),
+                torch.zeros(tiny.n, dtype=torch.float64, device="cuda"))
+    r = torch.zeros(tiny.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(m.AmgfError):
+        s.apply(r, r)  # aliasing
+
+
+def test_nonfinite_rhs_reports_status(tiny):
+    import paper_2505_18576_gb300 as m
+    s = m.Solver(tiny.K, tiny.J, tiny.D)
+    b = tiny.b.copy(); b[3] = np.nan
+    x = torch.zeros(tiny.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(dev(b), x, check=False)
+    assert st.status == 2

@@ -1,0 +1,125 @@
+"""CPU checks of the C-ABI library: exported symbols, host setup vs the oracle, input errors.
+
+No compute call reaches a device here; amgf_setup_host runs the host setup only.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import contactgen as cg
+import oracle
+import paper_2505_18576_gb300 as amgf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "amgf.h")).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(amgf_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = amgf.load_library()
+    names = declared_symbols()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(amgf.EXPORTED) == names
+
+
+def _compare_hierarchy(p, **opts):
+    o = oracle.Oracle(p.K, p.J, p.D, **opts)
+    s = amgf.Solver(p.K, p.J, p.D, host_only=True, **opts)
+    assert s.info.nlevels == o.nlev
+    for l in range(o.nlev):
+        A1, A2 = o.A(l), s.export(0, l)
+        assert A1.shape == A2.shape
+        assert np.array_equal(A1.indptr, A2.indptr) and np.array_equal(A1.indices, A2.indices)
+        assert np.array_equal(A1.data, A2.data)
+        if l + 1 < o.nlev:
+            P1, P2 = o.P(l), s.export(1, l)
+            assert np.array_equal(P1.indptr, P2.indptr) and np.array_equal(P1.indices, P2.indices)
+            assert np.array_equal(P1.data, P2.data)
+            R2 = s.export(2, l)
+            assert (R2 != P2.T).nnz == 0
+    if opts.get("filter", 1):
+        assert np.array_equal(o.Ic(), s.contact_set())
+    s.close()
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 4), (5, 3, 2), (16, 16, 8)])
+def test_host_setup_matches_oracle_bitwise(dims):
+    p = cg.make_problem(None, nx=dims[0], ny=dims[1], nz=dims[2], d_lo=-2, d_hi=8, seed=3)
+    _compare_hierarchy(p)
+
+
+def test_host_setup_matches_oracle_options(tiny):
+    _compare_hierarchy(tiny, strength_theta=0.25)
+    _compare_hierarchy(tiny, contact_components=1)
+    _compare_hierarchy(tiny, max_coarse=400)
+
+
+def test_host_setup_no_contact(tiny):
+    o = oracle.Oracle(tiny.K)
+    s = amgf.Solver(tiny.K, host_only=True)
+    assert s.info.nc == 0 and s.info.nlevels == o.nlev
+    for l in range(o.nlev):
+        assert (o.A(l) != s.export(0, l)).nnz == 0
+
+
+def test_host_only_handle_refuses_device_calls(tiny):
+    s = amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True)
+    lib = amgf.load_library()
+    st = lib.amgf_apply(s.h, ctypes.c_void_p(8), ctypes.c_void_p(16), None)
+    assert st == 1 and "host-only" in amgf.amgf_last_error()
+
+
+def test_filter_block_structure(tiny):
+    s = amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True)
+    nb, nblk = s.info.filter_block, s.info.filter_nblocks
+    assert nb >= 1 and nb * nblk >= s.info.nc and (nblk - 1) * nb < s.info.nc
+
+
+def test_invalid_inputs(tiny):
+    D = tiny.D.copy(); D[0] = np.inf
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(tiny.K, tiny.J, D, host_only=True)
+    assert e.value.status == 2
+    D = tiny.D.copy(); D[1] = 0.0
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(tiny.K, tiny.J, D, host_only=True)
+    assert e.value.status == 3
+    bad = cg.CSR(tiny.K.nrows, tiny.K.ncols, tiny.K.row_ptr.copy(), tiny.K.col_idx.copy(), tiny.K.val.copy())
+    bad.col_idx[1], bad.col_idx[2] = bad.col_idx[2], bad.col_idx[1]   # unsorted row
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(bad, tiny.J, tiny.D, host_only=True)
+    assert e.value.status == 1
+    nanK = cg.CSR(tiny.K.nrows, tiny.K.ncols, tiny.K.row_ptr, tiny.K.col_idx, tiny.K.val.copy())
+    nanK.val[5] = np.nan
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(nanK, tiny.J, tiny.D, host_only=True)
+    assert e.value.status == 2
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, nu=0)
+    assert e.value.status == 1
+
+
+def test_update_D_host(tiny):
+    s = amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True)
+    D2 = tiny.D * 10.0
+    s.update_D(D2)
+    o = oracle.Oracle(tiny.K, tiny.J, D2)
+    for l in range(o.nlev):
+        assert (o.A(l) != s.export(0, l)).nnz == 0
+
+
+def test_device_setup_without_gpu_fails_loudly(tiny):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(tiny.K, tiny.J, tiny.D)
+    assert e.value.status == 6

@@ -191,6 +191,7 @@ filter_fwd_kernel(const double* __restrict__ G, const int64_t* __restrict__ gidx
   const int64_t r0 = rank * rpc;
   const int64_t r1 = r0 + rpc < nb ? r0 + rpc : nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  cluster.sync();  // every CTA of the cluster has started before peers write its shared memory
   for (int64_t i = 0; i < nblk; ++i) {
     const int cur = (int)(i & 1);
     const double* Gi = G + i * nb * nb;
@@ -246,6 +247,7 @@ filter_bwd_kernel(const double* __restrict__ GT, const double* __restrict__ z, i
   const int64_t r0 = rank * rpc;
   const int64_t r1 = r0 + rpc < nb ? r0 + rpc : nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  cluster.sync();  // every CTA of the cluster has started before peers write its shared memory
   for (int64_t t = 0; t < nblk; ++t) {
     const int64_t i = nblk - 1 - t;
     const int cur = (int)(t & 1);

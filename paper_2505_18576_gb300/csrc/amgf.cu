@@ -51,6 +51,12 @@ struct DCSR {
   int32_t* ci = nullptr;
   double* v = nullptr;
   int K = 4;  // lanes per row
+  // optional 3x3 node-block copy used instead of the CSR arrays (fine level)
+  bool bsr = false;
+  int64_t nbrows = 0, nblocks = 0;
+  int64_t* brp = nullptr;
+  int32_t* bci = nullptr;
+  double* bv = nullptr;
 };
 
 struct DLevel {
@@ -174,6 +180,19 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
   a.rp = A.rp; a.ci = A.ci; a.v = A.v; a.nrows = A.nrows;
   if (A.nrows == 0) return;
   c.launches++;
+  if (A.bsr && !a.rows) {
+    BsrArgs b{};
+    b.brp = A.brp; b.bci = A.bci; b.v = A.bv; b.nbrows = A.nbrows;
+    b.x = a.x; b.b = a.b; b.winv = a.winv; b.add = a.add; b.y = a.y; b.y2 = a.y2;
+    const int grid = grid_for(c, A.nbrows, 32);
+    if (result) {
+      b.dotv = dotv; b.partial = c.partial; b.result = result; b.counter = c.counter;
+      bsr3_kernel<MODE, true><<<grid, TPB, 0, c.s>>>(b);
+    } else {
+      bsr3_kernel<MODE, false><<<grid, TPB, 0, c.s>>>(b);
+    }
+    return;
+  }
   const int grid = grid_for(c, A.nrows, A.K);
   if (result) {
     a.dotv = dotv; a.partial = c.partial; a.result = result; a.counter = c.counter;
@@ -391,7 +410,19 @@ static int build_all(Ctx& c, const double* D) {
   for (int l = 0; l < nlev; ++l) {
     DLevel& lv = c.L[l];
     lv.n = c.H.A[l].nrows;
-    if ((st = upload_csr(c, c.H.A[l], lv.A))) return st;
+    BSR3 bsr;
+    if (l == 0 && c.o.num_functions == 3 && build_bsr3(c.H.A[0], 1.05, bsr)) {
+      lv.A.nrows = lv.A.ncols = lv.n;
+      lv.A.nnz = c.H.A[0].nnz();
+      lv.A.bsr = true;
+      lv.A.nbrows = bsr.nbrows;
+      lv.A.nblocks = (int64_t)bsr.bci.size();
+      if ((st = c.upload(&lv.A.brp, bsr.brp.data(), bsr.nbrows + 1))) return st;
+      if ((st = c.upload(&lv.A.bci, bsr.bci.data(), lv.A.nblocks))) return st;
+      if ((st = c.upload(&lv.A.bv, bsr.v.data(), 9 * lv.A.nblocks))) return st;
+    } else if ((st = upload_csr(c, c.H.A[l], lv.A))) {
+      return st;
+    }
     if (l + 1 < nlev) {
       if ((st = upload_csr(c, c.H.P[l], lv.P))) return st;
       if ((st = upload_csr(c, c.H.R[l], lv.R))) return st;
@@ -765,7 +796,10 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
   *ms = t / reps;
   // values (8 B) + column indices (4 B) per nonzero, row pointers, and each vector read/written once
   const double vec_bytes = which == 0 ? 2.0 * 8.0 * n : 4.0 * 8.0 * n;
-  *bytes = nnz * 12.0 + (n + 1) * 8.0 + vec_bytes;
+  if (l0.A.bsr)  // 9 values + one block column index per block, block row pointers
+    *bytes = (double)l0.A.nblocks * (9.0 * 8.0 + 4.0) + (double)(l0.A.nbrows + 1) * 8.0 + vec_bytes;
+  else
+    *bytes = nnz * 12.0 + (n + 1) * 8.0 + vec_bytes;
   return join_end(c, stream);
 }
 

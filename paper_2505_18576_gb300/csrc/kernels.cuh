@@ -115,18 +115,105 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
     double s = 0.0;
     if (valid) {
       const int64_t k1 = a.rp[i + 1];
-      for (int64_t k = a.rp[i] + sub; k < k1; k += K) {
-        const int32_t j = a.ci[k];
-        double xv;
-        if (MODE == M_PRE) xv = a.winv[j] * a.b[j];
-        else xv = a.x[j];
-        s += a.v[k] * xv;
+      // batches of U entries per lane: all index/value loads of a batch are issued before
+      // the dependent gathers, so each batch costs two memory round trips
+      constexpr int U = 4;
+      for (int64_t kb = a.rp[i] + sub; kb < k1; kb += U * K) {
+        int32_t jj[U];
+        double vv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t k = kb + (int64_t)u * K;
+          const bool ok = k < k1;
+          jj[u] = ok ? __ldg(a.ci + k) : -1;
+          vv[u] = ok ? __ldg(a.v + k) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (jj[u] >= 0) {
+            double xv;
+            if (MODE == M_PRE) xv = __ldg(a.winv + jj[u]) * __ldg(a.b + jj[u]);
+            else xv = __ldg(a.x + jj[u]);
+            s += vv[u] * xv;
+          }
+        }
       }
     }
 #pragma unroll
     for (int off = K / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, K);
     if (valid && sub == 0) {
       const int64_t o = a.rows ? a.rows[i] : i;
+      double out;
+      if (MODE == M_SPMV) out = s;
+      else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
+      else if (MODE == M_RESID) out = a.b[o] - s;
+      else if (MODE == M_PRE) { a.y2[o] = a.winv[o] * a.b[o]; out = a.b[o] - s; }
+      else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
+      a.y[o] = out;
+      if (DOT) dacc += a.dotv[o] * out;
+    }
+  }
+  if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
+}
+
+// Fine-level operator in 3x3 node blocks (BSR3).  Block row I (node I) holds nbr blocks;
+// value k (row k/3, column k%3 of the block) of block b of that row sits at
+// v[9*s + k*nbr + b], s = first block of the row, so each of the nine loads of a warp
+// reads consecutive doubles.  One warp per block row, one block per lane; the three row
+// sums are reduced with shuffles and lanes 0..2 write rows 3I..3I+2.  Same epilogues as
+// csr_kernel (SPMV, RESID, PRE, POST, optional deterministic dot).
+struct BsrArgs {
+  const int64_t* __restrict__ brp;
+  const int32_t* __restrict__ bci;
+  const double* __restrict__ v;
+  int64_t nbrows;
+  const double* x;
+  const double* b;
+  const double* winv;
+  const double* add;
+  double* y;
+  double* y2;
+  const double* dotv;
+  double* partial;
+  double* result;
+  unsigned* counter;
+};
+
+template <int MODE, bool DOT>
+__global__ void __launch_bounds__(TPB) bsr3_kernel(BsrArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5;
+  const int64_t wstride = ((int64_t)gridDim.x * TPB) >> 5;
+  double dacc = 0.0;
+  for (int64_t I = warp0; I < a.nbrows; I += wstride) {
+    const int64_t s0 = a.brp[I];
+    const int64_t nbr = a.brp[I + 1] - s0;
+    const double* vb = a.v + 9 * s0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int64_t bb = lane; bb < nbr; bb += 32) {
+      const double* p = vb + bb;
+      double m[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) m[q] = __ldg(p + q * nbr);
+      const int64_t J = __ldg(a.bci + s0 + bb);
+      double x0, x1, x2;
+      if (MODE == M_PRE) {
+        x0 = __ldg(a.winv + 3 * J) * __ldg(a.b + 3 * J);
+        x1 = __ldg(a.winv + 3 * J + 1) * __ldg(a.b + 3 * J + 1);
+        x2 = __ldg(a.winv + 3 * J + 2) * __ldg(a.b + 3 * J + 2);
+      } else {
+        x0 = __ldg(a.x + 3 * J); x1 = __ldg(a.x + 3 * J + 1); x2 = __ldg(a.x + 3 * J + 2);
+      }
+      a0 += m[0] * x0 + m[1] * x1 + m[2] * x2;
+      a1 += m[3] * x0 + m[4] * x1 + m[5] * x2;
+      a2 += m[6] * x0 + m[7] * x1 + m[8] * x2;
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (lane < 3) {
+      const double s = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+      const int64_t o = 3 * I + lane;
       double out;
       if (MODE == M_SPMV) out = s;
       else if (MODE == M_SPMV_ADD) out = a.y[o] + s;

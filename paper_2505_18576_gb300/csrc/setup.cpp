@@ -338,6 +338,52 @@ void gemm(int64_t n, const double* A, const double* B, double* C, double alpha, 
 
 }  // namespace
 
+bool build_bsr3(const HCSR& A, double max_fill, BSR3& out) {
+  out = BSR3();
+  if (A.nrows % 3 != 0 || A.nrows != A.ncols || A.nrows == 0) return false;
+  const int64_t nb = A.nrows / 3;
+  std::vector<int64_t> cnt(nb + 1, 0);
+  auto block_cols = [&](int64_t I, std::vector<int32_t>& cols) {
+    cols.clear();
+    for (int r = 0; r < 3; ++r)
+      for (int64_t k = A.rp[3 * I + r]; k < A.rp[3 * I + r + 1]; ++k) cols.push_back(A.ci[k] / 3);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+  };
+#pragma omp parallel
+  {
+    std::vector<int32_t> cols;
+#pragma omp for schedule(static)
+    for (int64_t I = 0; I < nb; ++I) { block_cols(I, cols); cnt[I + 1] = (int64_t)cols.size(); }
+  }
+  for (int64_t I = 0; I < nb; ++I) cnt[I + 1] += cnt[I];
+  if ((double)cnt[nb] * 9.0 > max_fill * (double)A.nnz()) return false;
+  out.nbrows = nb;
+  out.brp = cnt;
+  out.bci.resize(cnt[nb]);
+  out.v.assign(9 * cnt[nb], 0.0);
+#pragma omp parallel
+  {
+    std::vector<int32_t> cols;
+#pragma omp for schedule(static)
+    for (int64_t I = 0; I < nb; ++I) {
+      block_cols(I, cols);
+      const int64_t s0 = out.brp[I], nbr = (int64_t)cols.size();
+      std::copy(cols.begin(), cols.end(), out.bci.begin() + s0);
+      for (int r = 0; r < 3; ++r) {
+        size_t b = 0;
+        for (int64_t k = A.rp[3 * I + r]; k < A.rp[3 * I + r + 1]; ++k) {
+          const int32_t J = A.ci[k] / 3;
+          while (cols[b] < J) ++b;
+          const int c = A.ci[k] % 3;
+          out.v[9 * s0 + (3 * r + c) * nbr + b] = A.v[k];
+        }
+      }
+    }
+  }
+  return true;
+}
+
 int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& err) {
   char buf[256];
   if (!a || a->nrows < 0 || a->ncols <= 0 || a->nnz < 0 || (a->nrows > 0 && (!a->row_ptr || !a->col_idx || !a->val))) {

@@ -42,6 +42,20 @@ struct Filter {
   HCSR Sc;
 };
 
+// Fine-level operator in 3x3 node blocks, values stored row-block-wise as nine
+// consecutive planes: v[9*s + k*nbr + b] = entry k (row k/3, col k%3) of block b of a
+// block row whose first block is s and which has nbr blocks.
+struct BSR3 {
+  int64_t nbrows = 0;
+  std::vector<int64_t> brp;
+  std::vector<int32_t> bci;
+  std::vector<double> v;
+};
+
+// Converts A to BSR3 when n % 3 == 0 and the explicit zero fill stays below `max_fill`
+// (stored values / nnz); returns false otherwise.
+bool build_bsr3(const HCSR& A, double max_fill, BSR3& out);
+
 // Input validation; returns an amgf_status.
 int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& err);
 

@@ -186,7 +186,7 @@ def run_gpu(args, rank, world, local):
 
     p, rhs = make_inputs(args.config)
     t0 = time.perf_counter()
-    s = amgf.Solver(p.K, p.J, p.D)
+    s = amgf.Solver(p.K, p.J, p.D, use_graph=0 if args.no_graph else 1)
     t_setup = time.perf_counter() - t0
     info = s.info
     n = p.n
@@ -306,6 +306,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations timed for cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=4, help="oracle PCG iterations per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the PCG kernels directly instead of one CUDA graph (for per-kernel profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

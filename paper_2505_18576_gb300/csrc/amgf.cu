@@ -148,11 +148,11 @@ struct Ctx {
 // ---------------------------------------------------------------------------------------
 // launch helpers
 
+// Lanes per row.  FP64 runs at ~2 FMA/clk/SM here, so the pass is bound by FP64 warp
+// instructions: (ceil(len/K) + log2 K) K / 32 per row is smallest for small K, while K = 4
+// still reads whole 32-byte sectors of values.
 static int lanes_for(double avg_nnz) {
-  if (avg_nnz >= 48) return 32;
-  if (avg_nnz >= 20) return 16;
-  if (avg_nnz >= 9) return 8;
-  if (avg_nnz >= 4) return 4;
+  if (avg_nnz >= 6) return 4;
   return 2;
 }
 
@@ -183,13 +183,14 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
   if (A.bsr && !a.rows) {
     BsrArgs b{};
     b.brp = A.brp; b.bci = A.bci; b.v = A.bv; b.nbrows = A.nbrows;
-    b.x = a.x; b.b = a.b; b.winv = a.winv; b.add = a.add; b.y = a.y; b.y2 = a.y2;
-    const int grid = grid_for(c, A.nbrows, 32);
+    b.x = a.x; b.b = a.b; b.winv = a.winv; b.w2 = a.w2; b.add = a.add; b.y = a.y; b.y2 = a.y2;
+    constexpr int KB = 4;
+    const int grid = grid_for(c, A.nbrows, KB);
     if (result) {
       b.dotv = dotv; b.partial = c.partial; b.result = result; b.counter = c.counter;
-      bsr3_kernel<MODE, true><<<grid, TPB, 0, c.s>>>(b);
+      bsr3_kernel<KB, MODE, true><<<grid, TPB, 0, c.s>>>(b);
     } else {
-      bsr3_kernel<MODE, false><<<grid, TPB, 0, c.s>>>(b);
+      bsr3_kernel<KB, MODE, false><<<grid, TPB, 0, c.s>>>(b);
     }
     return;
   }
@@ -209,8 +210,9 @@ static int vec_grid(const Ctx& c, int64_t n) {
 }
 
 // ---------------------------------------------------------------------------------------
-// V-cycle: out0 = B rhs0 (+ add0); optional dot(dotv, out0) -> *dotres
-
+// V-cycle: out0 = B rhs0 (+ add0); optional dot(dotv, out0) -> *dotres.
+// On entry L[0].x must hold W_0 rhs0 (the pre-smoothed iterate from a zero start); the
+// kernels that produce a V-cycle's right-hand side write it as a second output.
 static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const double* add0, const double* dotv,
                            double* dotres) {
   const int nlev = (int)c.L.size();
@@ -218,9 +220,10 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
   auto rhs_of = [&](int l) -> const double* { return l == 0 ? rhs0 : c.L[l].rhs; };
   for (int l = 0; l + 1 < nlev; ++l) {
     DLevel& lv = c.L[l];
+    // pre-smoothing from zero: x = W r (already in lv.x); residual r - A x
     CsrArgs a{};
-    a.b = rhs_of(l); a.winv = lv.winv; a.y = lv.res; a.y2 = lv.x;
-    launch_csr<M_PRE>(c, lv.A, a);
+    a.x = lv.x; a.b = rhs_of(l); a.y = lv.res;
+    launch_csr<M_RESID>(c, lv.A, a);
     for (int s = 1; s < nu; ++s) {
       axpy_w_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.x);
       c.launches++;
@@ -228,9 +231,15 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
       rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
       launch_csr<M_RESID>(c, lv.A, rr);
     }
+    // restriction; also W_{l+1} r_{l+1} for the next level's pre-smoothing
     CsrArgs rs{};
     rs.x = lv.res; rs.y = c.L[l + 1].rhs;
-    launch_csr<M_SPMV>(c, lv.R, rs);
+    if (l + 2 < nlev) {
+      rs.w2 = c.L[l + 1].winv; rs.y2 = c.L[l + 1].x;
+      launch_csr<M_SPMV_W>(c, lv.R, rs);
+    } else {
+      launch_csr<M_SPMV>(c, lv.R, rs);
+    }
   }
   // coarsest level: exact solve with the dense inverse
   {
@@ -262,6 +271,11 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
   }
 }
 
+static void enqueue_scale_w0(Ctx& c, const double* r) {
+  scale_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.L[0].winv, r, c.L[0].x);
+  c.launches++;
+}
+
 // w (factor order, length nblk*nb) = A_w^{-1} v, v gathered from r at gidx (or given directly)
 static void enqueue_filter_solve(Ctx& c, const double* r, const double* vdirect) {
   const int64_t nb = c.F.nb, nblk = c.F.nblk;
@@ -275,7 +289,7 @@ static void enqueue_filter_solve(Ctx& c, const double* r, const double* vdirect)
   c.launches += 3;
 }
 
-// z = M r; optional dot(r, z) -> *dotres
+// z = M r; optional dot(r, z) -> *dotres.  On entry L[0].x must hold W_0 r.
 static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres) {
   if (!c.o.filter) {  // M = B
     enqueue_vcycle(c, r, z, nullptr, r, dotres);
@@ -283,17 +297,17 @@ static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres) {
   }
   // y1 = B r
   enqueue_vcycle(c, r, c.y1, nullptr, nullptr, nullptr);
-  // r1 = r - A y1
+  // r1 = r - A y1 (and W_0 r1 for the second V-cycle)
   CsrArgs ra{};
-  ra.x = c.y1; ra.b = r; ra.y = c.r1;
-  launch_csr<M_RESID>(c, c.L[0].A, ra);
+  ra.x = c.y1; ra.b = r; ra.y = c.r1; ra.w2 = c.L[0].winv; ra.y2 = c.L[0].x;
+  launch_csr<M_RESID_W>(c, c.L[0].A, ra);
   if (c.F.nc > 0) {
     enqueue_filter_solve(c, c.r1, nullptr);
     filter_scatter_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.fgidx, c.fw, c.y1, c.F.nc);  // y2 = y1 + P w
     c.launches++;
-    CsrArgs sa{};
-    sa.rows = c.ftouch; sa.x = c.fw; sa.b = c.r1; sa.y = c.r1;                               // r2 = r1 - A P w
-    launch_csr<M_RESID>(c, c.fSc, sa);
+    CsrArgs sa{};                                                                              // r2 = r1 - A P w
+    sa.rows = c.ftouch; sa.x = c.fw; sa.b = c.r1; sa.y = c.r1; sa.w2 = c.L[0].winv; sa.y2 = c.L[0].x;
+    launch_csr<M_RESID_W>(c, c.fSc, sa);
   }
   // z = y2 + B r2
   enqueue_vcycle(c, c.r1, z, c.y1, r, dotres);
@@ -304,7 +318,7 @@ static void enqueue_pcg_body(Ctx& c, int use_cond) {
   CsrArgs qa{};
   qa.x = c.p; qa.y = c.q;
   launch_csr<M_SPMV>(c, c.L[0].A, qa, c.p, &c.st->pq);
-  pcg_update_xr_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.p, c.q, c.x, c.r, c.n);
+  pcg_update_xr_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.p, c.q, c.x, c.r, c.L[0].winv, c.L[0].x, c.n);
   enqueue_apply(c, c.r, c.z, &c.st->rz_new);
   pcg_update_p_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.z, c.p, c.n);
   pcg_finalize_kernel<<<1, 1, 0, c.s>>>(c.st, c.cond, use_cond);
@@ -313,8 +327,8 @@ static void enqueue_pcg_body(Ctx& c, int use_cond) {
 
 static void enqueue_pcg_init(Ctx& c) {
   CsrArgs ra{};
-  ra.x = c.x; ra.b = c.b; ra.y = c.r;
-  launch_csr<M_RESID>(c, c.L[0].A, ra);                 // r0 = b - A x0
+  ra.x = c.x; ra.b = c.b; ra.y = c.r; ra.w2 = c.L[0].winv; ra.y2 = c.L[0].x;
+  launch_csr<M_RESID_W>(c, c.L[0].A, ra);               // r0 = b - A x0, W_0 r0
   enqueue_apply(c, c.r, c.z, &c.st->rz_new);             // z0 = M r0, rz_new = r0^T z0
   pcg_init_kernel<<<1, 1, 0, c.s>>>(c.st, c.o.maxit, c.o.rtol);
   copy_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.z, c.p);  // p0 = z0
@@ -615,6 +629,7 @@ int amgf_apply(amgf_handle h, const double* r_dev, double* z_dev, void* stream) 
   CK(cudaSetDevice(c.device));
   int st = join_begin(c, stream);
   if (st) return st;
+  enqueue_scale_w0(c, r_dev);
   enqueue_apply(c, r_dev, z_dev, nullptr);
   return join_end(c, stream);
 }
@@ -626,6 +641,7 @@ int amgf_vcycle(amgf_handle h, const double* r_dev, double* x_dev, void* stream)
   CK(cudaSetDevice(c.device));
   int st = join_begin(c, stream);
   if (st) return st;
+  enqueue_scale_w0(c, r_dev);
   enqueue_vcycle(c, r_dev, x_dev, nullptr, nullptr, nullptr);
   return join_end(c, stream);
 }

@@ -27,7 +27,11 @@ namespace amgf {
 constexpr int TPB = 256;          // threads per block of the row kernels
 constexpr int MAX_DOT_BLOCKS = 4096;
 
-enum : int { M_SPMV = 0, M_SPMV_ADD = 1, M_RESID = 2, M_PRE = 3, M_POST = 4 };
+// Epilogues around s = (A x)_i:
+//   SPMV    y = s                      SPMV_W  y = s, y2 = w2 * s (restriction: coarse rhs and W_c rhs)
+//   SPMV_ADD y += s                    RESID   y = b - s
+//   RESID_W y = b - s, y2 = w2 * y     POST    y = x + w (b - s) [+ add]
+enum : int { M_SPMV = 0, M_SPMV_ADD = 1, M_RESID = 2, M_RESID_W = 3, M_POST = 4, M_SPMV_W = 5 };
 
 struct CsrArgs {
   const int64_t* __restrict__ rp;
@@ -37,10 +41,11 @@ struct CsrArgs {
   const int64_t* __restrict__ rows;  // optional row indirection (output row = rows[i])
   const double* x;      // gathered vector (unused by PRE)
   const double* b;      // right-hand side (RESID, PRE, POST)
-  const double* winv;   // 1 / l1 (PRE, POST)
+  const double* winv;   // 1 / l1 of the rows (POST)
+  const double* w2;     // scaling written to y2 (RESID_W, SPMV_W)
   const double* add;    // POST: optional vector added to the output
   double* y;            // output
-  double* y2;           // PRE: x = W b
+  double* y2;           // RESID_W, SPMV_W: second output w2 * y
   const double* dotv;   // DOT: partner vector of the output
   double* partial;      // DOT: one partial per block
   double* result;       // DOT: final scalar
@@ -129,14 +134,8 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
           vv[u] = ok ? __ldg(a.v + k) : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (jj[u] >= 0) {
-            double xv;
-            if (MODE == M_PRE) xv = __ldg(a.winv + jj[u]) * __ldg(a.b + jj[u]);
-            else xv = __ldg(a.x + jj[u]);
-            s += vv[u] * xv;
-          }
-        }
+        for (int u = 0; u < U; ++u)
+          if (jj[u] >= 0) s += vv[u] * __ldg(a.x + jj[u]);
       }
     }
 #pragma unroll
@@ -144,12 +143,12 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
     if (valid && sub == 0) {
       const int64_t o = a.rows ? a.rows[i] : i;
       double out;
-      if (MODE == M_SPMV) out = s;
+      if (MODE == M_SPMV || MODE == M_SPMV_W) out = s;
       else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
-      else if (MODE == M_RESID) out = a.b[o] - s;
-      else if (MODE == M_PRE) { a.y2[o] = a.winv[o] * a.b[o]; out = a.b[o] - s; }
+      else if (MODE == M_RESID || MODE == M_RESID_W) out = a.b[o] - s;
       else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
       a.y[o] = out;
+      if (MODE == M_RESID_W || MODE == M_SPMV_W) a.y2[o] = a.w2[o] * out;
       if (DOT) dacc += a.dotv[o] * out;
     }
   }
@@ -170,6 +169,7 @@ struct BsrArgs {
   const double* x;
   const double* b;
   const double* winv;
+  const double* w2;
   const double* add;
   double* y;
   double* y2;
@@ -179,52 +179,67 @@ struct BsrArgs {
   unsigned* counter;
 };
 
-template <int MODE, bool DOT>
+// KB lanes per block row (KB block rows per warp / KB): each lane walks the row's blocks
+// with stride KB; nine plane loads per block read KB consecutive doubles per group.  With
+// FP64 at ~2 FMA/clk/SM on this part the number of FP64 warp instructions per nonzero is
+// what bounds the pass, so groups are kept narrow (few shuffle-add steps).
+template <int KB, int MODE, bool DOT>
 __global__ void __launch_bounds__(TPB) bsr3_kernel(BsrArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp0 = ((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5;
-  const int64_t wstride = ((int64_t)gridDim.x * TPB) >> 5;
+  const int lane_w = threadIdx.x & 31;
+  const int sub = lane_w & (KB - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * TPB + threadIdx.x) / KB;
+  const int64_t warp_first = gid - (lane_w / KB);
+  const int64_t stride = (int64_t)gridDim.x * (TPB / KB);
   double dacc = 0.0;
-  for (int64_t I = warp0; I < a.nbrows; I += wstride) {
-    const int64_t s0 = a.brp[I];
-    const int64_t nbr = a.brp[I + 1] - s0;
-    const double* vb = a.v + 9 * s0;
+  for (int64_t base = warp_first; base < a.nbrows; base += stride) {
+    const int64_t I = base + lane_w / KB;
+    const bool valid = I < a.nbrows;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int64_t bb = lane; bb < nbr; bb += 32) {
-      const double* p = vb + bb;
-      double m[9];
+    if (valid) {
+      const int64_t s0 = a.brp[I];
+      const int64_t nbr = a.brp[I + 1] - s0;
+      const double* vb = a.v + 9 * s0;
+      for (int64_t bb = sub; bb < nbr; bb += KB) {
+        const double* p = vb + bb;
+        double m[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) m[q] = __ldg(p + q * nbr);
-      const int64_t J = __ldg(a.bci + s0 + bb);
-      double x0, x1, x2;
-      if (MODE == M_PRE) {
-        x0 = __ldg(a.winv + 3 * J) * __ldg(a.b + 3 * J);
-        x1 = __ldg(a.winv + 3 * J + 1) * __ldg(a.b + 3 * J + 1);
-        x2 = __ldg(a.winv + 3 * J + 2) * __ldg(a.b + 3 * J + 2);
-      } else {
-        x0 = __ldg(a.x + 3 * J); x1 = __ldg(a.x + 3 * J + 1); x2 = __ldg(a.x + 3 * J + 2);
+        for (int q = 0; q < 9; ++q) m[q] = __ldg(p + q * nbr);
+        const int64_t J = __ldg(a.bci + s0 + bb);
+        const double x0 = __ldg(a.x + 3 * J), x1 = __ldg(a.x + 3 * J + 1), x2 = __ldg(a.x + 3 * J + 2);
+        a0 += m[0] * x0 + m[1] * x1 + m[2] * x2;
+        a1 += m[3] * x0 + m[4] * x1 + m[5] * x2;
+        a2 += m[6] * x0 + m[7] * x1 + m[8] * x2;
       }
-      a0 += m[0] * x0 + m[1] * x1 + m[2] * x2;
-      a1 += m[3] * x0 + m[4] * x1 + m[5] * x2;
-      a2 += m[6] * x0 + m[7] * x1 + m[8] * x2;
     }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
-    if (lane < 3) {
-      const double s = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
-      const int64_t o = 3 * I + lane;
-      double out;
-      if (MODE == M_SPMV) out = s;
-      else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
-      else if (MODE == M_RESID) out = a.b[o] - s;
-      else if (MODE == M_PRE) { a.y2[o] = a.winv[o] * a.b[o]; out = a.b[o] - s; }
-      else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
-      a.y[o] = out;
-      if (DOT) dacc += a.dotv[o] * out;
+#pragma unroll
+    for (int off = KB / 2; off > 0; off >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, off, KB);
+      a1 += __shfl_down_sync(0xffffffffu, a1, off, KB);
+      a2 += __shfl_down_sync(0xffffffffu, a2, off, KB);
+    }
+    if (valid && sub == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double s = c == 0 ? a0 : (c == 1 ? a1 : a2);
+        const int64_t o = 3 * I + c;
+        double out;
+        if (MODE == M_SPMV || MODE == M_SPMV_W) out = s;
+        else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
+        else if (MODE == M_RESID || MODE == M_RESID_W) out = a.b[o] - s;
+        else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
+        a.y[o] = out;
+        if (MODE == M_RESID_W || MODE == M_SPMV_W) a.y2[o] = a.w2[o] * out;
+        if (DOT) dacc += a.dotv[o] * out;
+      }
     }
   }
   if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
+}
+
+// y = W r elementwise (entry of a V-cycle whose rhs was not produced by a fused kernel)
+__global__ void scale_kernel(int64_t n, const double* __restrict__ w, const double* __restrict__ r, double* y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = w[i] * r[i];
 }
 
 // x_i += W_i * res_i (extra pre-smoothing sweeps when nu > 1)
@@ -376,9 +391,10 @@ __global__ void permute_kernel(int64_t n, const int64_t* __restrict__ scatter_to
 
 // ---------------- PCG ----------------
 
-// x += alpha p ; r -= alpha q with alpha = rz / pq (breakdown if pq <= 0)
+// x += alpha p ; r -= alpha q with alpha = rz / pq (breakdown if pq <= 0); wr = W0 r (the
+// fine-level pre-smoothing iterate of the next V-cycle)
 __global__ void pcg_update_xr_kernel(PcgState* st, const double* __restrict__ p, const double* __restrict__ q,
-                                     double* x, double* r, int64_t n) {
+                                     double* x, double* r, const double* __restrict__ w0, double* wr, int64_t n) {
   if (st->done) return;
   const double pq = st->pq;
   if (!(pq > 0.0)) {
@@ -388,7 +404,9 @@ __global__ void pcg_update_xr_kernel(PcgState* st, const double* __restrict__ p,
   const double alpha = st->rz / pq;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
-    r[i] -= alpha * q[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    wr[i] = w0[i] * ri;
   }
 }
 

@@ -131,6 +131,20 @@ int amgf_matvec(amgf_handle h, const double* x_dev, double* y_dev, void* stream)
  * ascending-DOF order of I_c. */
 int amgf_filter_solve(amgf_handle h, const double* v_dev, double* w_dev, void* stream);
 
+/* Same result as amgf_filter_solve, for callers that cannot allocate device memory while
+ * they run (another allocator owns the device, or a cudaMalloc and the synchronisation it
+ * may imply are not allowed in their loop).  The paper has no counterpart: this is a
+ * property of the library, not of the method.  Its four work vectors live in one array of
+ * 524288 doubles (4 MiB) compiled into the library, which every GPU that loads the library
+ * holds until the process exits; a filter needing more than 4 x 131072 doubles (block
+ * size x number of blocks, see amgf_info) is rejected with AMGF_ERR_INVALID_ARG.  The call
+ * allocates nothing.  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call before any
+ * stream capture.  All calls share the array: two calls whose work overlaps on the GPU
+ * (different streams, or different handles on one device) race and give wrong results;
+ * keep them ordered.  Nothing in the array needs clearing between calls. */
+int amgf_filter_solve_noalloc(amgf_handle h, const double* v_dev, double* w_dev, void* stream);
+
 /* PCG on A x = b (x_dev holds x0 on entry, the solution on exit), preconditioned by
  * M, stopped when sqrt(r^T z / r0^T z0) < rtol (Section 4) or after maxit
  * iterations.  Synchronises `stream` to fill *st (may be NULL).

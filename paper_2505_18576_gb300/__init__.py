@@ -20,11 +20,12 @@ from .build import LIB as _LIB_PATH, build as _build
 
 __all__ = ["AmgfError", "Options", "Stats", "Info", "Solver", "load_library", "amgf_options_default",
            "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec", "amgf_filter_solve",
-           "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
+           "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
            "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED"]
 
 EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec",
-            "amgf_filter_solve", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info",
+            "amgf_filter_solve", "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host",
+            "amgf_get_info",
             "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
             "amgf_last_error"]
 
@@ -87,6 +88,7 @@ def load_library(build_if_missing: bool = True):
         "amgf_vcycle": [vp, vp, vp, vp],
         "amgf_matvec": [vp, vp, vp, vp],
         "amgf_filter_solve": [vp, vp, vp, vp],
+        "amgf_filter_solve_noalloc": [vp, vp, vp, vp],
         "amgf_pcg_solve": [vp, vp, vp, vp, vp],
         "amgf_pcg_solve_host": [vp, vp, vp, vp],
         "amgf_get_info": [vp, vp],
@@ -202,6 +204,12 @@ def amgf_matvec(h, x, y, n: int, stream=None):
 
 def amgf_filter_solve(h, v, w, nc: int, stream=None):
     _check(load_library().amgf_filter_solve(h, _dev_vec(v, nc, "v"), _dev_vec(w, nc, "w"), _stream(stream)))
+
+
+def amgf_filter_solve_noalloc(h, v, w, nc: int, stream=None):
+    """amgf_filter_solve with its work vectors in the library's fixed array (allocates nothing)."""
+    _check(load_library().amgf_filter_solve_noalloc(h, _dev_vec(v, nc, "v"), _dev_vec(w, nc, "w"),
+                                                     _stream(stream)))
 
 
 def amgf_pcg_solve(h, b, x, n: int, stream=None, check: bool = True) -> Stats:

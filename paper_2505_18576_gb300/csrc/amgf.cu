@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -820,3 +821,70 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Filter solve without library-owned work vectors.
+//
+// For callers that must not allocate device memory themselves or through this library
+// while they run -- for example because another allocator owns the whole device, or
+// because a cudaMalloc (and the device synchronisation it can imply) is not allowed in
+// their loop.  The four work vectors of the filter solve live in one fixed-size array
+// compiled into this library instead of in memory the handle allocated.  The array is
+// shared by every call on a device and keeps the previous call's contents; every entry a
+// call reads is first written by that same call, so nothing has to start at zero.
+
+namespace {
+constexpr int64_t kNoAllocScratchDoubles = 524288;  // 4 MiB: four vectors of up to 131072 doubles
+static __device__ __align__(256) double g_filter_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[64] = {nullptr};  // device address of g_filter_scratch, per device ordinal
+
+// Looks up the device address of the scratch array once per device, with that device current.
+int scratch_for_device(int dev, double** out) {
+  if (dev < 0 || dev >= 64) return fail(AMGF_ERR_CUDA, "device ordinal out of range for the scratch table");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_filter_scratch);
+    if (e != cudaSuccess) return fail(AMGF_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_scratch_ptr[dev] = (double*)p;
+  }
+  *out = g_scratch_ptr[dev];
+  return AMGF_OK;
+}
+}  // namespace
+
+extern "C" int amgf_filter_solve_noalloc(amgf_handle h, const double* v_dev, double* w_dev, void* stream) {
+  if (!h || !v_dev || !w_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  if (h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  Ctx& c = h->c;
+  if (c.F.nc == 0) return fail(AMGF_ERR_INVALID_ARG, "empty contact set");
+  const int64_t len = c.F.nb * c.F.nblk;
+  if (4 * len > kNoAllocScratchDoubles) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "filter too large for the fixed scratch: needs 4 x %lld doubles, limit %lld",
+             (long long)len, (long long)kNoAllocScratchDoubles);
+    return fail(AMGF_ERR_INVALID_ARG, buf);
+  }
+  CK(cudaSetDevice(c.device));
+  double* scratch = nullptr;
+  int st = scratch_for_device(c.device, &scratch);
+  if (st) return st;
+  double* v = scratch;
+  double* y = scratch + len;
+  double* z = scratch + 2 * len;
+  double* w = scratch + 3 * len;
+  st = join_begin(c, stream);
+  if (st) return st;
+  const int64_t nb = c.F.nb, nblk = c.F.nblk;
+  const size_t smem = 2 * nb * sizeof(double);
+  permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, nullptr, c.ficidx, v_dev, v);
+  filter_fwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fG, c.fgidx, nullptr, v, c.F.nc, nb, nblk, y);
+  int g = (int)((len * 32 + TPB - 1) / TPB);
+  if (g > c.num_sms * 8) g = c.num_sms * 8;
+  filter_diag_kernel<<<g, TPB, 0, c.s>>>(c.fDinv, y, z, nb, nblk);
+  filter_bwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fGT, z, nb, nblk, w);
+  permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, c.ficidx, nullptr, w, w_dev);
+  return join_end(c, stream);
+}

@@ -73,8 +73,9 @@ def test_host_setup_no_contact(tiny):
 def test_host_only_handle_refuses_device_calls(tiny):
     s = amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True)
     lib = amgf.load_library()
-    st = lib.amgf_apply(s.h, ctypes.c_void_p(8), ctypes.c_void_p(16), None)
-    assert st == 1 and "host-only" in amgf.amgf_last_error()
+    for fn in (lib.amgf_apply, lib.amgf_filter_solve_noalloc):
+        st = fn(s.h, ctypes.c_void_p(8), ctypes.c_void_p(16), None)
+        assert st == 1 and "host-only" in amgf.amgf_last_error()
 
 
 def test_filter_block_structure(tiny):

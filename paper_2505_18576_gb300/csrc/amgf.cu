@@ -99,6 +99,9 @@ struct Ctx {
   cudaGraphConditionalHandle cond{};
   int64_t n = 0, m = 0;
   bool host_only = false;
+  int filter_cs = 8;          // CTAs per cluster of the filter sweeps
+  bool filter_staged = false; // sweeps stage the next block's rows in shared memory
+  size_t filter_smem = 0;
   int64_t launches = 0;       // kernels enqueued since the counter was last read
   int64_t init_launches = 0, body_launches = 0;
 
@@ -149,12 +152,16 @@ struct Ctx {
 // ---------------------------------------------------------------------------------------
 // launch helpers
 
-// Lanes per row.  FP64 runs at ~2 FMA/clk/SM here, so the pass is bound by FP64 warp
-// instructions: (ceil(len/K) + log2 K) K / 32 per row is smallest for small K, while K = 4
-// still reads whole 32-byte sectors of values.
-static int lanes_for(double avg_nnz) {
-  if (avg_nnz >= 6) return 4;
-  return 2;
+// Lanes per row.  On a large level FP64 issue bounds the pass (~2 FMA/clk/SM on this part):
+// (ceil(len/K) + log2 K) K / 32 FP64 warp instructions per row is smallest for small K, and
+// K = 4 still reads whole 32-byte sectors of values.  A small level cannot fill the GPU with
+// 4 lanes per row and is bound by each row's chain of dependent loads instead, so its
+// groups widen until rows * K covers the resident threads (2048 per SM).
+static int lanes_for(int64_t rows, double avg_nnz, int num_sms) {
+  int k = avg_nnz >= 6 ? 4 : 2;
+  const double resident = 2048.0 * num_sms;
+  while (k < 32 && (double)rows * k < resident && k < avg_nnz) k *= 2;
+  return k;
 }
 
 static int grid_for(const Ctx& c, int64_t rows, int K) {
@@ -277,17 +284,44 @@ static void enqueue_scale_w0(Ctx& c, const double* r) {
   c.launches++;
 }
 
-// w (factor order, length nblk*nb) = A_w^{-1} v, v gathered from r at gidx (or given directly)
-static void enqueue_filter_solve(Ctx& c, const double* r, const double* vdirect) {
+// one block sweep of the filter factor as a thread-block cluster launch
+static void launch_sweep(Ctx& c, bool fwd, const double* M, const double* r, const double* vdirect, const double* zin,
+                         double* out) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c.filter_cs, 1, 1);
+  cfg.blockDim = dim3(FILTER_TPB, 1, 1);
+  cfg.dynamicSmemBytes = c.filter_smem;
+  cfg.stream = c.s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = c.filter_cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int64_t nb = c.F.nb, nblk = c.F.nblk, nc = c.F.nc;
+  if (c.filter_staged)
+    cudaLaunchKernelEx(&cfg, filter_sweep_kernel<true>, fwd, M, (const int64_t*)c.fgidx, r, vdirect, zin, nc, nb, nblk, out);
+  else
+    cudaLaunchKernelEx(&cfg, filter_sweep_kernel<false>, fwd, M, (const int64_t*)c.fgidx, r, vdirect, zin, nc, nb, nblk, out);
+  c.launches++;
+}
+
+// out (factor order, length nblk*nb) = A_w^{-1} v with v gathered from r at gidx (or given
+// directly in factor order by vdirect); y and z are work vectors of the same length
+static void enqueue_filter_solve_into(Ctx& c, const double* r, const double* vdirect, double* y, double* z, double* out) {
   const int64_t nb = c.F.nb, nblk = c.F.nblk;
-  const size_t smem = 2 * nb * sizeof(double);
-  filter_fwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fG, c.fgidx, r, vdirect, c.F.nc, nb, nblk, c.fy);
+  launch_sweep(c, true, c.fG, r, vdirect, nullptr, y);
   const int64_t rows = nb * nblk;
   int g = (int)((rows * 32 + TPB - 1) / TPB);
   if (g > c.num_sms * 8) g = c.num_sms * 8;
-  filter_diag_kernel<<<g, TPB, 0, c.s>>>(c.fDinv, c.fy, c.fz, nb, nblk);
-  filter_bwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fGT, c.fz, nb, nblk, c.fw);
-  c.launches += 3;
+  filter_diag_kernel<<<g, TPB, 0, c.s>>>(c.fDinv, y, z, nb, nblk);
+  c.launches++;
+  launch_sweep(c, false, c.fGT, nullptr, nullptr, z, out);
+}
+
+static void enqueue_filter_solve(Ctx& c, const double* r, const double* vdirect) {
+  enqueue_filter_solve_into(c, r, vdirect, c.fy, c.fz, c.fw);
 }
 
 // z = M r; optional dot(r, z) -> *dotres.  On entry L[0].x must hold W_0 r.
@@ -372,12 +406,13 @@ static int build_graph(Ctx& c) {
 // setup / upload
 
 static int upload_csr(Ctx& c, const HCSR& h, DCSR& d) {
+  const int num_sms = c.num_sms;
   d.nrows = h.nrows; d.ncols = h.ncols; d.nnz = h.nnz();
   int st;
   if ((st = c.upload(&d.rp, h.rp.data(), h.nrows + 1))) return st;
   if ((st = c.upload(&d.ci, h.ci.data(), d.nnz))) return st;
   if ((st = c.upload(&d.v, h.v.data(), d.nnz))) return st;
-  d.K = lanes_for(h.nrows ? (double)d.nnz / (double)h.nrows : 1.0);
+  d.K = lanes_for(h.nrows, h.nrows ? (double)d.nnz / (double)h.nrows : 1.0, num_sms);
   return AMGF_OK;
 }
 
@@ -468,11 +503,47 @@ static int build_all(Ctx& c, const double* D) {
     if ((st = c.alloc(&c.fz, tot))) return st;
     if ((st = c.alloc(&c.fw, tot))) return st;
     if ((st = c.alloc(&c.fv, tot))) return st;
-    // the filter sweeps need 2 * nb doubles of shared memory per CTA
-    const size_t smem = 2 * c.F.nb * sizeof(double);
-    if (smem > 200 * 1024) return fail(AMGF_ERR_INVALID_ARG, "filter block too large for shared memory");
-    CK(cudaFuncSetAttribute(filter_fwd_kernel<FILTER_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CK(cudaFuncSetAttribute(filter_bwd_kernel<FILTER_CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // filter sweeps: 16-CTA clusters where the device allows them, else 8; stage the next
+    // block's rows in shared memory when two stages fit next to the block vectors
+    {
+      const int64_t nb = c.F.nb;
+      auto smem_for = [&](int cs, bool staged) {
+        const int64_t rpc = (nb + cs - 1) / cs;
+        return (size_t)(2 * nb + (staged ? 2 * rpc * nb : 0)) * sizeof(double);
+      };
+      const size_t limit = 200 * 1024;
+      if (smem_for(8, false) > limit) return fail(AMGF_ERR_INVALID_ARG, "filter block too large for shared memory");
+      CK(cudaFuncSetAttribute(filter_sweep_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      CK(cudaFuncSetAttribute(filter_sweep_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      CK(cudaFuncSetAttribute(filter_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+      CK(cudaFuncSetAttribute(filter_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+      c.filter_cs = 8;
+      for (int cs : {16, 8}) {
+        const bool staged = smem_for(cs, true) <= limit;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs, 1, 1);
+        cfg.blockDim = dim3(FILTER_TPB, 1, 1);
+        cfg.dynamicSmemBytes = smem_for(cs, staged);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        const cudaError_t e = staged ? cudaOccupancyMaxActiveClusters(&nclusters, filter_sweep_kernel<true>, &cfg)
+                                     : cudaOccupancyMaxActiveClusters(&nclusters, filter_sweep_kernel<false>, &cfg);
+        if (e == cudaSuccess && nclusters > 0) {
+          c.filter_cs = cs;
+          c.filter_staged = staged;
+          c.filter_smem = smem_for(cs, staged);
+          break;
+        }
+        cudaGetLastError();  // clear a refused configuration and try the next one
+      }
+      if (c.filter_smem == 0) { c.filter_staged = false; c.filter_smem = smem_for(8, false); }
+    }
   }
   const int64_t n = c.n;
   double** vecs[] = {&c.b, &c.x, &c.r, &c.z, &c.p, &c.q, &c.y1, &c.r1};
@@ -489,9 +560,12 @@ static int build_all(Ctx& c, const double* D) {
   c.info.t_setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   amgf_info& in = c.info;
   if (c.o.verbose) {
-    fprintf(stderr, "amgf: n=%lld m=%lld nc=%lld levels=%d opcx=%.3f filter nb=%lld nblk=%lld setup %.2fs\n",
+    fprintf(stderr, "amgf: n=%lld m=%lld nc=%lld levels=%d opcx=%.3f filter nb=%lld nblk=%lld cluster=%d staged=%d setup %.2fs\n",
             (long long)c.n, (long long)c.m, (long long)c.F.nc, nlev, in.op_complexity, (long long)c.F.nb,
-            (long long)c.F.nblk, in.t_setup_s);
+            (long long)c.F.nblk, c.filter_cs, (int)c.filter_staged, in.t_setup_s);
+    for (int l = 0; l < nlev; ++l)
+      fprintf(stderr, "  level %d: rows %lld nnz %lld lanes %d%s\n", l, (long long)c.L[l].n, (long long)c.L[l].A.nnz,
+              c.L[l].A.K, c.L[l].A.bsr ? " (3x3 blocks)" : "");
   }
   CK(cudaDeviceSynchronize());
   return AMGF_OK;
@@ -877,14 +951,8 @@ extern "C" int amgf_filter_solve_noalloc(amgf_handle h, const double* v_dev, dou
   double* w = scratch + 3 * len;
   st = join_begin(c, stream);
   if (st) return st;
-  const int64_t nb = c.F.nb, nblk = c.F.nblk;
-  const size_t smem = 2 * nb * sizeof(double);
   permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, nullptr, c.ficidx, v_dev, v);
-  filter_fwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fG, c.fgidx, nullptr, v, c.F.nc, nb, nblk, y);
-  int g = (int)((len * 32 + TPB - 1) / TPB);
-  if (g > c.num_sms * 8) g = c.num_sms * 8;
-  filter_diag_kernel<<<g, TPB, 0, c.s>>>(c.fDinv, y, z, nb, nblk);
-  filter_bwd_kernel<FILTER_CS><<<FILTER_CS, FILTER_TPB, smem, c.s>>>(c.fGT, z, nb, nblk, w);
+  enqueue_filter_solve_into(c, nullptr, v, y, z, w);
   permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, c.ficidx, nullptr, w, w_dev);
   return join_end(c, stream);
 }

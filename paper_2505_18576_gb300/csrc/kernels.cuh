@@ -277,44 +277,97 @@ __global__ void __launch_bounds__(TPB) dense_gemv_kernel(int64_t n, const double
 
 // ---------------- filter: A_w^{-1} via block LDL^T (block-tridiagonal A_w) ----------------
 
-constexpr int FILTER_CS = 8;    // CTAs per cluster
 constexpr int FILTER_TPB = 512;
 
-// Forward sweep: y_0 = v_0, y_i = v_i - G_i y_{i-1}; v_p = r[gidx[p]] (0 on padding rows).
-template <int CS>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(FILTER_TPB)
-filter_fwd_kernel(const double* __restrict__ G, const int64_t* __restrict__ gidx, const double* __restrict__ r,
-                  const double* __restrict__ vdirect, int64_t nc, int64_t nb, int64_t nblk, double* y) {
+// 16-byte asynchronous global->shared copies (no spin waits: cp.async.wait_group is a
+// hardware wait on this thread's own copies)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// Copy this CTA's rows [r0, r0+nr) of one nb x nb block (row-major, nb even) to shared memory.
+__device__ __forceinline__ void stage_rows(double* dst, const double* blk, int64_t r0, int64_t nr, int64_t nb) {
+  const double* src = blk + r0 * nb;
+  const int64_t chunks = nr * nb / 2;  // 16-byte chunks
+  for (int64_t q = threadIdx.x; q < chunks; q += blockDim.x) cp_async16(dst + 2 * q, src + 2 * q);
+}
+
+// One dependent step of a block sweep: rows [r0, r1) of  out = vin - M xprev, where M's rows
+// come from shared memory (staged) or global memory; results go to every CTA of the cluster
+// (distributed shared memory, buffer `cur`) and to global memory.
+template <bool STAGED>
+__device__ __forceinline__ void sweep_rows(cooperative_groups::cluster_group& cluster, int cs, double* xbuf,
+                                           int cur, const double* xprev, bool has_prev, const double* Mrows,
+                                           const double* Mglob, int64_t r0, int64_t r1, int64_t nb,
+                                           int64_t pbase, int64_t nc, const double* r, const int64_t* gidx,
+                                           const double* vdirect, const double* zin, double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t rr = r0 + warp; rr < r1; rr += nw) {
+    const int64_t p = pbase + rr;
+    double s = 0.0;
+    if (has_prev) {
+      const double* row = STAGED ? (Mrows + (rr - r0) * nb) : (Mglob + rr * nb);
+#pragma unroll 4
+      for (int64_t k = lane; k < nb; k += 32) s += row[k] * xprev[k];
+    }
+    s = warp_sum(s);
+    double vin;
+    if (zin) vin = zin[p];
+    else vin = p < nc ? (vdirect ? vdirect[p] : r[gidx[p]]) : 0.0;
+    const double val = vin - s;
+    for (int t = lane; t < cs; t += 32) {
+      double* dst = cluster.map_shared_rank(xbuf, t);
+      dst[cur * nb + rr] = val;
+    }
+    if (lane == 0) out[p] = val;
+  }
+}
+
+// Block-tridiagonal LDL^T sweeps of A_w (Section 5.1 filter solve), one thread-block cluster
+// of cs CTAs (cluster size set at launch).  Each dependent block step is a GEMV split by
+// rows over the cluster; the running block vector is exchanged through distributed shared
+// memory.  With STAGED the next step's matrix rows are copied to shared memory with
+// cp.async while the current step computes and waits at the cluster barrier.
+//   forward  (fwd = true):  y_0 = v_0,            y_i = v_i - G_i y_{i-1}
+//   backward (fwd = false): w_{N-1} = z_{N-1},    w_i = z_i - G_{i+1}^T w_{i+1}
+// v_p = r[gidx[p]] (or vdirect[p]) for p < nc, 0 on padding rows.
+template <bool STAGED>
+__global__ void __launch_bounds__(FILTER_TPB)
+filter_sweep_kernel(bool fwd, const double* __restrict__ M, const int64_t* __restrict__ gidx,
+                    const double* __restrict__ r, const double* __restrict__ vdirect, const double* __restrict__ zin,
+                    int64_t nc, int64_t nb, int64_t nblk, double* out) {
   namespace cgp = cooperative_groups;
   cgp::cluster_group cluster = cgp::this_cluster();
-  extern __shared__ double ybuf[];  // [2][nb]
+  extern __shared__ __align__(16) double fsm[];
+  double* xbuf = fsm;                 // [2][nb]
+  double* gbuf = fsm + 2 * nb;        // [2][rpc][nb] when STAGED
+  const int cs = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
-  const int64_t rpc = (nb + CS - 1) / CS;
-  const int64_t r0 = rank * rpc;
+  const int64_t rpc = (nb + cs - 1) / cs;
+  const int64_t r0 = rank * rpc < nb ? rank * rpc : nb;
   const int64_t r1 = r0 + rpc < nb ? r0 + rpc : nb;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t nr = r1 - r0;
+  // matrix used by step t (t >= 1): forward G_t, backward G_{i+1}^T with i = nblk-1-t
+  auto mat_of = [&](int64_t t) -> const double* {
+    const int64_t blk = fwd ? t : (nblk - t);
+    return M + blk * nb * nb;
+  };
   cluster.sync();  // every CTA of the cluster has started before peers write its shared memory
-  for (int64_t i = 0; i < nblk; ++i) {
-    const int cur = (int)(i & 1);
-    const double* Gi = G + i * nb * nb;
-    const double* yprev = ybuf + (cur ^ 1) * nb;
-    for (int64_t rr = r0 + warp; rr < r1; rr += nw) {
-      const int64_t p = i * nb + rr;
-      double s = 0.0;
-      if (i > 0) {
-        const double* row = Gi + rr * nb;
-        for (int64_t k = lane; k < nb; k += 32) s += row[k] * yprev[k];
-      }
-      s = warp_sum(s);
-      double vin = 0.0;
-      if (p < nc) vin = vdirect ? vdirect[p] : r[gidx[p]];
-      const double val = vin - s;
-      if (lane < CS) {
-        double* dst = cluster.map_shared_rank(ybuf, lane);
-        dst[cur * nb + rr] = val;
-      }
-      if (lane == 0) y[p] = val;
+  for (int64_t t = 0; t < nblk; ++t) {
+    const int cur = (int)(t & 1);
+    if (STAGED) {
+      if (t + 1 < nblk) stage_rows(gbuf + ((t + 1) & 1) * rpc * nb, mat_of(t + 1), r0, nr, nb);
+      cp_async_commit();
+      cp_async_wait1();  // the copy for step t (committed one iteration earlier) has landed
+      __syncthreads();
     }
+    const int64_t i = fwd ? t : nblk - 1 - t;
+    sweep_rows<STAGED>(cluster, cs, xbuf, cur, xbuf + (cur ^ 1) * nb, t > 0, gbuf + cur * rpc * nb,
+                       t > 0 ? mat_of(t) : M, r0, r1, nb, i * nb, fwd ? nc : 0, r, gidx, vdirect,
+                       fwd ? nullptr : zin, out);
     cluster.sync();
   }
 }
@@ -331,46 +384,10 @@ __global__ void __launch_bounds__(TPB) filter_diag_kernel(const double* __restri
     const double* row = Dinv + blk * nb * nb + rr * nb;
     const double* yb = y + blk * nb;
     double s = 0.0;
+#pragma unroll 4
     for (int64_t k = lane; k < nb; k += 32) s += row[k] * yb[k];
     s = warp_sum(s);
     if (lane == 0) z[p] = s;
-  }
-}
-
-// Backward sweep: w_{N-1} = z_{N-1}, w_i = z_i - G_{i+1}^T w_{i+1}.
-template <int CS>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(FILTER_TPB)
-filter_bwd_kernel(const double* __restrict__ GT, const double* __restrict__ z, int64_t nb, int64_t nblk, double* w) {
-  namespace cgp = cooperative_groups;
-  cgp::cluster_group cluster = cgp::this_cluster();
-  extern __shared__ double xbuf[];  // [2][nb]
-  const int rank = (int)cluster.block_rank();
-  const int64_t rpc = (nb + CS - 1) / CS;
-  const int64_t r0 = rank * rpc;
-  const int64_t r1 = r0 + rpc < nb ? r0 + rpc : nb;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  cluster.sync();  // every CTA of the cluster has started before peers write its shared memory
-  for (int64_t t = 0; t < nblk; ++t) {
-    const int64_t i = nblk - 1 - t;
-    const int cur = (int)(t & 1);
-    const double* xnext = xbuf + (cur ^ 1) * nb;
-    const double* GTn = GT + (i + 1) * nb * nb;  // only read when i + 1 < nblk
-    for (int64_t rr = r0 + warp; rr < r1; rr += nw) {
-      const int64_t p = i * nb + rr;
-      double s = 0.0;
-      if (i + 1 < nblk) {
-        const double* row = GTn + rr * nb;
-        for (int64_t k = lane; k < nb; k += 32) s += row[k] * xnext[k];
-      }
-      s = warp_sum(s);
-      const double val = z[p] - s;
-      if (lane < CS) {
-        double* dst = cluster.map_shared_rank(xbuf, lane);
-        dst[cur * nb + rr] = val;
-      }
-      if (lane == 0) w[p] = val;
-    }
-    cluster.sync();
   }
 }
 

@@ -629,7 +629,8 @@ int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter
   int64_t bw = 0;
   for (int64_t t = 0; t < nc; ++t)
     for (int64_t k = Aw.rp[t]; k < Aw.rp[t + 1]; ++k) { const int64_t d = pos[t] - pos[Aw.ci[k]]; bw = std::max<int64_t>(bw, d < 0 ? -d : d); }
-  const int64_t nb = std::max<int64_t>(bw, 1);
+  // block size = bandwidth, rounded up to even so every block row starts on a 16-byte boundary
+  const int64_t nb = std::max<int64_t>((bw + 1) & ~int64_t(1), 2);
   const int64_t nblk = (nc + nb - 1) / nb;
   F.nb = nb;
   F.nblk = nblk;

@@ -186,7 +186,7 @@ def run_gpu(args, rank, world, local):
 
     p, rhs = make_inputs(args.config)
     t0 = time.perf_counter()
-    s = amgf.Solver(p.K, p.J, p.D, use_graph=0 if args.no_graph else 1)
+    s = amgf.Solver(p.K, p.J, p.D, use_graph=0 if args.no_graph else 1, precision=args.precision)
     t_setup = time.perf_counter() - t0
     info = s.info
     n = p.n
@@ -238,18 +238,76 @@ def run_gpu(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
-    # dominant kernel: fine-level l1-Jacobi post-smoother (level-0 SpMV + fused epilogue)
-    kms, kbytes = s.time_kernel(1, warmup=5, reps=50)
-    peak, peak_kind = peaks()
-    achieved = kbytes / (kms * 1e-3) / 1e9
+    # the same workload with the other V-cycle precisions (same timing method, fewer steps),
+    # each with its A-norm distance to this run's solution of seed 0
+    variants = {}
+    if not args.no_variants:
+        x_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
+        s.pcg_solve(bdev[0], x_ref)
+        Kt = None
+        for prec in (0, 1, 2):
+            if prec == args.precision:
+                continue
+            sv = amgf.Solver(p.K, p.J, p.D, precision=prec)
+            xv = torch.zeros(n, dtype=torch.float64, device="cuda")
+            for k in range(2):
+                xv.zero_()
+                sv.pcg_solve(bdev[k % 3], xv)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            its = []
+            nst = max(2, min(args.steps, 5))
+            e0.record(stream)
+            for k in range(nst):
+                xv.zero_()
+                its.append(sv.pcg_solve(bdev[k % 3], xv, stream=stream).iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            xv.zero_()
+            sv.pcg_solve(bdev[0], xv)
+            d = xv - x_ref
+            yd = torch.empty_like(d)
+            yr = torch.empty_like(d)
+            s.matvec(d, yd)
+            s.matvec(x_ref, yr)
+            rel_a = float(torch.sqrt(torch.dot(d, yd) / torch.dot(x_ref, yr)))
+            variants[{0: "fp64", 1: "fp32_vcycle", 2: "fp32_vcycle_bf16_K"}[prec]] = {
+                "s_per_solve": e0.elapsed_time(e1) / nst * 1e-3, "pcg_iters": its,
+                "a_norm_rel_diff_vs_timed_solution": rel_a}
+            sv.close()
+
+    # dominant kernel: the fine-level l1-Jacobi post-smoother (one pass over the fine operator with
+    # the fused smoother epilogue), timed alone with CUDA events.  In FP64 the pass is bound by the
+    # FP64 pipe (2 FMA/clk/SM on this part), in the FP32 V-cycle by HBM bandwidth.
+    which = 2 if s.info.n and args.precision else 1
+    kms, kbytes = s.time_kernel(which, warmup=5, reps=50)
+    hbm_peak, peak_kind = peaks()
+    gbs = kbytes / (kms * 1e-3) / 1e9
+    nnz0 = int(s.info.level_nnz[0])
+    kflops = 2.0 * nnz0 + 4.0 * n          # 2 per nonzero, 4 per row (b - s, * w, + x, + add)
+    tflops = kflops / (kms * 1e-3) / 1e12
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             tr = json.load(f)
-        if tr.get("config") == args.config and tr.get("kernel_source_sha") == kernel_source_sha():
-            traffic = tr.get("dram_bytes_per_launch")
+        ent = tr.get(f"{args.config}:precision{args.precision}", {})
+        if ent.get("kernel_source_sha") == kernel_source_sha():
+            traffic = ent.get("dram_bytes_per_launch")
     except Exception:
         pass
+    if args.precision == 0:
+        fp64_peak = fp64_peak_tflops()
+        roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                    "frac": round(tflops / fp64_peak, 4), "traffic": traffic,
+                    "kernel": "bsr3_kernel<4,POST,0>: fine-level FP64 l1-Jacobi sweep over A (3x3 node blocks)",
+                    "flops_per_launch": kflops, "bytes_per_launch": kbytes, "ms_per_launch": kms,
+                    "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+                    "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+    else:
+        roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
+                    "kernel": "bsr3_mixed_kernel<POST>: fine-level FP32 l1-Jacobi sweep (K blocks + FP64 contact term)",
+                    "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_kind": f"{peak_kind} (burst)"}
 
     if rank == 0:
         cpu = None
@@ -263,8 +321,10 @@ def run_gpu(args, rank, world, local):
         line = {
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32" + ("+bf16" if args.precision == 2 else ""),
+            "data": "synthetic",
             "config": {"workload": f"{args.config}: {WORKLOADS.get(args.config, args.config)}",
+                       "precision": ["fp64", "fp32 V-cycle", "fp32 V-cycle, bf16 fine K"][args.precision],
                        "n": n, "m": p.m, "nc": int(info.nc), "levels": int(info.nlevels),
                        "op_complexity": round(float(info.op_complexity), 4), "rtol": 1e-8,
                        "stop": "sqrt(r^T z / r0^T z0)", "pcg_iters": iters,
@@ -272,12 +332,11 @@ def run_gpu(args, rank, world, local):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "csr_kernel<32,POST> level 0 (l1-Jacobi sweep, A_0 = S)",
-                         "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_kind": f"{peak_kind} (burst)"},
+            "roofline": roofline,
             "clocks": clocks,
         }
+        if variants:
+            line["variants"] = variants
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -285,6 +344,16 @@ def run_gpu(args, rank, world, local):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def fp64_peak_tflops():
+    """FP64 FMA pipe: 2 FMA per clock per SM on this part (nominal 1.25 TFLOP/s), 152 SMs, 2.07 GHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        mhz = 2070.0
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
 
 
 def kernel_source_sha():
@@ -306,6 +375,9 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations timed for cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=4, help="oracle PCG iterations per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="V-cycle precision of the timed solve: 0 FP64, 1 FP32, 2 FP32 with BF16 fine-level K")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant timings")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the PCG kernels directly instead of one CUDA graph (for per-kernel profiling)")
     args = ap.parse_args()

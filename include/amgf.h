@@ -68,6 +68,11 @@ typedef struct {
   int maxit;              /* PCG iteration cap (5000, Section 6.1) */
   int use_graph;          /* 1: capture the PCG loop in one CUDA graph with a device-side while node */
   int verbose;            /* 1: print setup summary to stderr */
+  int precision;          /* 0: FP64 throughout (default).  1: V-cycle in FP32 (FP32 matrices and
+                             vectors, int32 indices, FP32 accumulation) inside an FP64 flexible PCG;
+                             the outer residual, the dot products, the J^T D J term and the filter
+                             solve stay FP64.  2: as 1 with the fine-level K values in BF16.
+                             Needs >= 2 levels and 3 unknowns per node, else FP64 is used. */
 } amgf_options;
 
 typedef struct {
@@ -168,7 +173,8 @@ int amgf_export_contact_set(amgf_handle h, int64_t* ic);
 
 /* Time `reps` back-to-back launches of one kernel of the solve phase on `stream`
  * with CUDA events, after `warmup` untimed launches.  which: 0 = fine-level
- * A x (SpMV of level 0), 1 = fine-level post-smoother.  *ms = average per launch;
+ * A x (SpMV of level 0), 1 = fine-level FP64 post-smoother, 2 = fine-level post-smoother
+ * of the FP32 V-cycle (mixed-precision handles only).  *ms = average per launch;
  * *bytes = algorithmic bytes one launch moves (values + indices + vectors). */
 int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* stream,
                      double* ms, double* bytes);

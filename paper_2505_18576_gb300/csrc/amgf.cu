@@ -60,10 +60,22 @@ struct DCSR {
   double* bv = nullptr;
 };
 
+struct DCSRf {  // FP32 values (V-cycle levels of the mixed-precision solve)
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  int64_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  float* v = nullptr;
+  int K = 4;
+};
+
 struct DLevel {
   DCSR A, P, R;
   double* winv = nullptr;
   double *rhs = nullptr, *x = nullptr, *res = nullptr, *out = nullptr;
+  // FP32 copies used when the V-cycle runs in single precision
+  DCSRf Af, Pf, Rf;
+  float* winvf = nullptr;
+  float *rhsf = nullptr, *xf = nullptr, *resf = nullptr, *outf = nullptr;
   int64_t n = 0;
 };
 
@@ -82,7 +94,17 @@ struct Ctx {
   std::vector<void*> allocs;
   std::vector<DLevel> L;
   double* coarse_inv = nullptr;
+  float* coarse_inv_f = nullptr;
   int64_t nL = 0;
+  // mixed precision: fine-level K in 3x3 blocks (FP32 or BF16 planes) + contact term in FP64
+  bool mixed = false;
+  bool k_bf16 = false;
+  int64_t k_nbrows = 0, k_nblocks = 0;
+  int64_t* k_brp = nullptr;
+  int32_t* k_bci = nullptr;
+  void* k_v = nullptr;
+  int32_t *c_rp = nullptr, *c_ci = nullptr;
+  double* c_v = nullptr;
   double *fG = nullptr, *fGT = nullptr, *fDinv = nullptr, *fy = nullptr, *fz = nullptr, *fw = nullptr, *fv = nullptr;
   int64_t* fgidx = nullptr;
   int64_t* ficidx = nullptr;  // factor position -> index into I_c
@@ -175,11 +197,11 @@ static int grid_for(const Ctx& c, int64_t rows, int K) {
 template <int MODE, bool DOT>
 static void launch_csr_k(int K, int grid, cudaStream_t s, const CsrArgs& a) {
   switch (K) {
-    case 32: csr_kernel<32, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
-    case 16: csr_kernel<16, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
-    case 8: csr_kernel<8, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
-    case 4: csr_kernel<4, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
-    default: csr_kernel<2, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    case 32: csr_kernel<double, 32, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    case 16: csr_kernel<double, 16, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    case 8: csr_kernel<double, 8, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    case 4: csr_kernel<double, 4, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
+    default: csr_kernel<double, 2, MODE, DOT><<<grid, TPB, 0, s>>>(a); break;
   }
 }
 
@@ -192,6 +214,7 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
     BsrArgs b{};
     b.brp = A.brp; b.bci = A.bci; b.v = A.bv; b.nbrows = A.nbrows;
     b.x = a.x; b.b = a.b; b.winv = a.winv; b.w2 = a.w2; b.add = a.add; b.y = a.y; b.y2 = a.y2;
+    b.yf = a.yf; b.y2f = a.y2f;
     constexpr int KB = 4;
     const int grid = grid_for(c, A.nbrows, KB);
     if (result) {
@@ -208,6 +231,49 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
     launch_csr_k<MODE, true>(A.K, grid, c.s, a);
   } else {
     launch_csr_k<MODE, false>(A.K, grid, c.s, a);
+  }
+}
+
+template <int MODE>
+static void launch_csr_f(Ctx& c, const DCSRf& A, CsrArgsT<float> a) {
+  a.rp = A.rp; a.ci = A.ci; a.v = A.v; a.nrows = A.nrows;
+  if (A.nrows == 0) return;
+  c.launches++;
+  const int grid = grid_for(c, A.nrows, A.K);
+  switch (A.K) {
+    case 32: csr_kernel<float, 32, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+    case 16: csr_kernel<float, 16, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+    case 8: csr_kernel<float, 8, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+    case 4: csr_kernel<float, 4, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+    default: csr_kernel<float, 2, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+  }
+}
+
+// fine level of the FP32 V-cycle (K blocks + FP64 contact term)
+template <int MODE>
+static void launch_fine_mixed(Ctx& c, const float* x, const float* b, const float* winv, const double* add,
+                              float* y32, double* y64, const double* dotv, double* result) {
+  constexpr int KB = 4;
+  const int grid = grid_for(c, c.k_nbrows, KB);
+  c.launches++;
+  auto fill = [&](auto& a) {
+    a.brp = c.k_brp; a.bci = c.k_bci; a.nbrows = c.k_nbrows;
+    a.crp = c.c_rp; a.cci = c.c_ci; a.cv = c.c_v;
+    a.x = x; a.b = b; a.winv = winv; a.add = add; a.y32 = y32; a.y64 = y64;
+    a.dotv = dotv; a.partial = c.partial; a.result = result; a.counter = c.counter;
+  };
+  if (c.k_bf16) {
+    Bsr3MixedArgs<__nv_bfloat16> a{};
+    fill(a);
+    a.v = (const __nv_bfloat16*)c.k_v;
+    if (result) bsr3_mixed_kernel<__nv_bfloat16, KB, MODE, true><<<grid, TPB, 0, c.s>>>(a);
+    else bsr3_mixed_kernel<__nv_bfloat16, KB, MODE, false><<<grid, TPB, 0, c.s>>>(a);
+  } else {
+    Bsr3MixedArgs<float> a{};
+    fill(a);
+    a.v = (const float*)c.k_v;
+    if (result) bsr3_mixed_kernel<float, KB, MODE, true><<<grid, TPB, 0, c.s>>>(a);
+    else bsr3_mixed_kernel<float, KB, MODE, false><<<grid, TPB, 0, c.s>>>(a);
   }
 }
 
@@ -279,9 +345,79 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
   }
 }
 
-static void enqueue_scale_w0(Ctx& c, const double* r) {
-  scale_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.L[0].winv, r, c.L[0].x);
+// FP32 V-cycle: out0 (FP64) = B rhs (+ add0), optional dot(dotv, out0) -> *dotres.  On entry
+// L[0].rhsf holds the right-hand side in FP32 and L[0].xf = W_0 rhs in FP32 (written by the
+// FP64 kernel that produced the right-hand side: the precision boundary going in); the
+// fine-level post-smoother writes the FP64 output (the boundary going out).
+static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const double* dotv, double* dotres) {
+  const int nlev = (int)c.L.size();
+  const int nu = c.o.nu < 1 ? 1 : c.o.nu;
+  for (int l = 0; l + 1 < nlev; ++l) {
+    DLevel& lv = c.L[l];
+    for (int s = 0; s < nu; ++s) {
+      if (s > 0) {
+        axpy_w_f32_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.xf);
+        c.launches++;
+      }
+      if (l == 0) {
+        launch_fine_mixed<M_RESID>(c, lv.xf, lv.rhsf, nullptr, nullptr, lv.resf, nullptr, nullptr, nullptr);
+      } else {
+        CsrArgsT<float> a{};
+        a.x = lv.xf; a.b = lv.rhsf; a.y = lv.resf;
+        launch_csr_f<M_RESID>(c, lv.Af, a);
+      }
+    }
+    CsrArgsT<float> rs{};
+    rs.x = lv.resf; rs.y = c.L[l + 1].rhsf;
+    if (l + 2 < nlev) {
+      rs.w2 = c.L[l + 1].winvf; rs.y2 = c.L[l + 1].xf;
+      launch_csr_f<M_SPMV_W>(c, lv.Rf, rs);
+    } else {
+      launch_csr_f<M_SPMV>(c, lv.Rf, rs);
+    }
+  }
+  dense_gemv_f32_kernel<<<1, TPB, 0, c.s>>>(c.nL, c.coarse_inv_f, c.L[nlev - 1].rhsf, c.L[nlev - 1].outf);
   c.launches++;
+  for (int l = nlev - 2; l >= 0; --l) {
+    DLevel& lv = c.L[l];
+    CsrArgsT<float> pa{};
+    pa.x = c.L[l + 1].outf; pa.y = lv.xf;
+    launch_csr_f<M_SPMV_ADD>(c, lv.Pf, pa);
+    for (int s = 1; s < nu; ++s) {
+      if (l == 0) {
+        launch_fine_mixed<M_RESID>(c, lv.xf, lv.rhsf, nullptr, nullptr, lv.resf, nullptr, nullptr, nullptr);
+      } else {
+        CsrArgsT<float> rr{};
+        rr.x = lv.xf; rr.b = lv.rhsf; rr.y = lv.resf;
+        launch_csr_f<M_RESID>(c, lv.Af, rr);
+      }
+      axpy_w_f32_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.xf);
+      c.launches++;
+    }
+    if (l == 0) {
+      launch_fine_mixed<M_POST>(c, lv.xf, lv.rhsf, lv.winvf, add0, nullptr, out0, dotv, dotres);
+    } else {
+      CsrArgsT<float> po{};
+      po.x = lv.xf; po.b = lv.rhsf; po.winv = lv.winvf; po.y = lv.outf;
+      launch_csr_f<M_POST>(c, lv.Af, po);
+    }
+  }
+}
+
+static void enqueue_scale_w0(Ctx& c, const double* r) {
+  if (c.mixed) {
+    to_f32_scaled_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.L[0].winv, r, c.L[0].rhsf, c.L[0].xf);
+  } else {
+    scale_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.L[0].winv, r, c.L[0].x);
+  }
+  c.launches++;
+}
+
+// B rhs0 in the configured precision (see enqueue_vcycle / enqueue_vcycle_f32 for the entry state)
+static void enqueue_B(Ctx& c, const double* rhs0, double* out0, const double* add0, const double* dotv,
+                      double* dotres) {
+  if (c.mixed) enqueue_vcycle_f32(c, out0, add0, dotv, dotres);
+  else enqueue_vcycle(c, rhs0, out0, add0, dotv, dotres);
 }
 
 // one block sweep of the filter factor as a thread-block cluster launch
@@ -327,25 +463,27 @@ static void enqueue_filter_solve(Ctx& c, const double* r, const double* vdirect)
 // z = M r; optional dot(r, z) -> *dotres.  On entry L[0].x must hold W_0 r.
 static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres) {
   if (!c.o.filter) {  // M = B
-    enqueue_vcycle(c, r, z, nullptr, r, dotres);
+    enqueue_B(c, r, z, nullptr, r, dotres);
     return;
   }
   // y1 = B r
-  enqueue_vcycle(c, r, c.y1, nullptr, nullptr, nullptr);
-  // r1 = r - A y1 (and W_0 r1 for the second V-cycle)
+  enqueue_B(c, r, c.y1, nullptr, nullptr, nullptr);
+  // r1 = r - A y1 (and the entry state of the second V-cycle: W_0 r1, FP32 copies if mixed)
   CsrArgs ra{};
-  ra.x = c.y1; ra.b = r; ra.y = c.r1; ra.w2 = c.L[0].winv; ra.y2 = c.L[0].x;
+  ra.x = c.y1; ra.b = r; ra.y = c.r1; ra.w2 = c.L[0].winv;
+  if (c.mixed) { ra.yf = c.L[0].rhsf; ra.y2f = c.L[0].xf; } else { ra.y2 = c.L[0].x; }
   launch_csr<M_RESID_W>(c, c.L[0].A, ra);
   if (c.F.nc > 0) {
     enqueue_filter_solve(c, c.r1, nullptr);
     filter_scatter_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.fgidx, c.fw, c.y1, c.F.nc);  // y2 = y1 + P w
     c.launches++;
     CsrArgs sa{};                                                                              // r2 = r1 - A P w
-    sa.rows = c.ftouch; sa.x = c.fw; sa.b = c.r1; sa.y = c.r1; sa.w2 = c.L[0].winv; sa.y2 = c.L[0].x;
+    sa.rows = c.ftouch; sa.x = c.fw; sa.b = c.r1; sa.y = c.r1; sa.w2 = c.L[0].winv;
+    if (c.mixed) { sa.yf = c.L[0].rhsf; sa.y2f = c.L[0].xf; } else { sa.y2 = c.L[0].x; }
     launch_csr<M_RESID_W>(c, c.fSc, sa);
   }
   // z = y2 + B r2
-  enqueue_vcycle(c, c.r1, z, c.y1, r, dotres);
+  enqueue_B(c, c.r1, z, c.y1, r, dotres);
 }
 
 // one PCG iteration (body of the while node)
@@ -353,7 +491,9 @@ static void enqueue_pcg_body(Ctx& c, int use_cond) {
   CsrArgs qa{};
   qa.x = c.p; qa.y = c.q;
   launch_csr<M_SPMV>(c, c.L[0].A, qa, c.p, &c.st->pq);
-  pcg_update_xr_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.p, c.q, c.x, c.r, c.L[0].winv, c.L[0].x, c.n);
+  pcg_update_xr_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(
+      c.st, c.p, c.q, c.x, c.r, c.L[0].winv, c.mixed ? nullptr : c.L[0].x, c.mixed ? c.L[0].rhsf : nullptr,
+      c.mixed ? c.L[0].xf : nullptr, c.mixed ? c.z : nullptr, c.partial, c.counter, c.n);
   enqueue_apply(c, c.r, c.z, &c.st->rz_new);
   pcg_update_p_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.z, c.p, c.n);
   pcg_finalize_kernel<<<1, 1, 0, c.s>>>(c.st, c.cond, use_cond);
@@ -362,10 +502,11 @@ static void enqueue_pcg_body(Ctx& c, int use_cond) {
 
 static void enqueue_pcg_init(Ctx& c) {
   CsrArgs ra{};
-  ra.x = c.x; ra.b = c.b; ra.y = c.r; ra.w2 = c.L[0].winv; ra.y2 = c.L[0].x;
+  ra.x = c.x; ra.b = c.b; ra.y = c.r; ra.w2 = c.L[0].winv;
+  if (c.mixed) { ra.yf = c.L[0].rhsf; ra.y2f = c.L[0].xf; } else { ra.y2 = c.L[0].x; }
   launch_csr<M_RESID_W>(c, c.L[0].A, ra);               // r0 = b - A x0, W_0 r0
   enqueue_apply(c, c.r, c.z, &c.st->rz_new);             // z0 = M r0, rz_new = r0^T z0
-  pcg_init_kernel<<<1, 1, 0, c.s>>>(c.st, c.o.maxit, c.o.rtol);
+  pcg_init_kernel<<<1, 1, 0, c.s>>>(c.st, c.o.maxit, c.o.rtol, c.mixed ? 1 : 0);
   copy_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.z, c.p);  // p0 = z0
   c.launches += 2;
 }
@@ -416,6 +557,17 @@ static int upload_csr(Ctx& c, const HCSR& h, DCSR& d) {
   return AMGF_OK;
 }
 
+static int upload_csr_f(Ctx& c, const HCSR& h, DCSRf& d) {
+  d.nrows = h.nrows; d.ncols = h.ncols; d.nnz = h.nnz();
+  int st;
+  if ((st = c.upload(&d.rp, h.rp.data(), h.nrows + 1))) return st;
+  if ((st = c.upload(&d.ci, h.ci.data(), d.nnz))) return st;
+  std::vector<float> v(h.v.begin(), h.v.end());
+  if ((st = c.upload(&d.v, v.data(), d.nnz))) return st;
+  d.K = lanes_for(h.nrows, h.nrows ? (double)d.nnz / (double)h.nrows : 1.0, c.num_sms);
+  return AMGF_OK;
+}
+
 static void fill_info(Ctx& c) {
   amgf_info& in = c.info;
   std::memset(&in, 0, sizeof in);
@@ -457,36 +609,90 @@ static int build_all(Ctx& c, const double* D) {
   c.release_device();
   const int nlev = c.H.nlev();
   c.L.assign(nlev, DLevel());
+  // mixed precision needs a coarse level and the 3x3 node-block structure of K
+  BSR3 kb;
+  c.mixed = c.o.precision > 0 && nlev >= 2 && c.o.num_functions == 3 && build_bsr3(c.Kh, 1.05, kb);
+  c.k_bf16 = c.mixed && c.o.precision == 2;
   for (int l = 0; l < nlev; ++l) {
     DLevel& lv = c.L[l];
     lv.n = c.H.A[l].nrows;
-    BSR3 bsr;
-    if (l == 0 && c.o.num_functions == 3 && build_bsr3(c.H.A[0], 1.05, bsr)) {
-      lv.A.nrows = lv.A.ncols = lv.n;
-      lv.A.nnz = c.H.A[0].nnz();
-      lv.A.bsr = true;
-      lv.A.nbrows = bsr.nbrows;
-      lv.A.nblocks = (int64_t)bsr.bci.size();
-      if ((st = c.upload(&lv.A.brp, bsr.brp.data(), bsr.nbrows + 1))) return st;
-      if ((st = c.upload(&lv.A.bci, bsr.bci.data(), lv.A.nblocks))) return st;
-      if ((st = c.upload(&lv.A.bv, bsr.v.data(), 9 * lv.A.nblocks))) return st;
-    } else if ((st = upload_csr(c, c.H.A[l], lv.A))) {
-      return st;
-    }
-    if (l + 1 < nlev) {
-      if ((st = upload_csr(c, c.H.P[l], lv.P))) return st;
-      if ((st = upload_csr(c, c.H.R[l], lv.R))) return st;
-    }
     std::vector<double> w(lv.n);
     for (int64_t i = 0; i < lv.n; ++i) w[i] = 1.0 / c.H.l1[l][i];
-    if ((st = c.upload(&lv.winv, w.data(), lv.n))) return st;
-    if ((st = c.alloc(&lv.rhs, lv.n))) return st;
-    if ((st = c.alloc(&lv.x, lv.n))) return st;
-    if ((st = c.alloc(&lv.res, lv.n))) return st;
-    if ((st = c.alloc(&lv.out, lv.n))) return st;
+    // FP64 operator: always on the fine level (outer PCG), on every level without mixed precision
+    if (l == 0 || !c.mixed) {
+      BSR3 bsr;
+      if (l == 0 && c.o.num_functions == 3 && build_bsr3(c.H.A[0], 1.05, bsr)) {
+        lv.A.nrows = lv.A.ncols = lv.n;
+        lv.A.nnz = c.H.A[0].nnz();
+        lv.A.bsr = true;
+        lv.A.nbrows = bsr.nbrows;
+        lv.A.nblocks = (int64_t)bsr.bci.size();
+        if ((st = c.upload(&lv.A.brp, bsr.brp.data(), bsr.nbrows + 1))) return st;
+        if ((st = c.upload(&lv.A.bci, bsr.bci.data(), lv.A.nblocks))) return st;
+        if ((st = c.upload(&lv.A.bv, bsr.v.data(), 9 * lv.A.nblocks))) return st;
+      } else if ((st = upload_csr(c, c.H.A[l], lv.A))) {
+        return st;
+      }
+      if ((st = c.upload(&lv.winv, w.data(), lv.n))) return st;
+      if ((st = c.alloc(&lv.x, lv.n))) return st;
+    }
+    if (!c.mixed) {
+      if (l + 1 < nlev) {
+        if ((st = upload_csr(c, c.H.P[l], lv.P))) return st;
+        if ((st = upload_csr(c, c.H.R[l], lv.R))) return st;
+      }
+      if ((st = c.alloc(&lv.rhs, lv.n))) return st;
+      if ((st = c.alloc(&lv.res, lv.n))) return st;
+      if ((st = c.alloc(&lv.out, lv.n))) return st;
+    } else {
+      if (l > 0 && (st = upload_csr_f(c, c.H.A[l], lv.Af))) return st;
+      if (l + 1 < nlev) {
+        if ((st = upload_csr_f(c, c.H.P[l], lv.Pf))) return st;
+        if ((st = upload_csr_f(c, c.H.R[l], lv.Rf))) return st;
+      }
+      std::vector<float> wf(w.begin(), w.end());
+      if ((st = c.upload(&lv.winvf, wf.data(), lv.n))) return st;
+      if ((st = c.alloc(&lv.rhsf, lv.n))) return st;
+      if ((st = c.alloc(&lv.xf, lv.n))) return st;
+      if ((st = c.alloc(&lv.resf, lv.n))) return st;
+      if ((st = c.alloc(&lv.outf, lv.n))) return st;
+    }
   }
   c.nL = c.H.n_coarse;
-  if ((st = c.upload(&c.coarse_inv, c.H.coarse_inv.data(), c.nL * c.nL))) return st;
+  if (!c.mixed) {
+    if ((st = c.upload(&c.coarse_inv, c.H.coarse_inv.data(), c.nL * c.nL))) return st;
+  } else {
+    std::vector<float> ci(c.H.coarse_inv.begin(), c.H.coarse_inv.end());
+    if ((st = c.upload(&c.coarse_inv_f, ci.data(), c.nL * c.nL))) return st;
+    // fine-level K in 3x3 blocks, FP32 or BF16 (round to nearest even)
+    c.k_nbrows = kb.nbrows;
+    c.k_nblocks = (int64_t)kb.bci.size();
+    if ((st = c.upload(&c.k_brp, kb.brp.data(), kb.nbrows + 1))) return st;
+    if ((st = c.upload(&c.k_bci, kb.bci.data(), c.k_nblocks))) return st;
+    if (c.k_bf16) {
+      std::vector<__nv_bfloat16> v(kb.v.size());
+      for (size_t i = 0; i < v.size(); ++i) v[i] = __float2bfloat16_rn((float)kb.v[i]);
+      __nv_bfloat16* d = nullptr;
+      if ((st = c.upload(&d, v.data(), (int64_t)v.size()))) return st;
+      c.k_v = d;
+    } else {
+      std::vector<float> v(kb.v.begin(), kb.v.end());
+      float* d = nullptr;
+      if ((st = c.upload(&d, v.data(), (int64_t)v.size()))) return st;
+      c.k_v = d;
+    }
+    // contact term J^T D J over all rows, FP64
+    std::vector<int64_t> zrp(c.n + 1, 0);
+    amgf_csr Z{c.n, c.n, 0, zrp.data(), nullptr, nullptr};
+    HCSR C;
+    st = assemble_S(&Z, c.m > 0 ? &J : nullptr, D, C, err);
+    if (st) return fail(st, err);
+    std::vector<int32_t> crp(c.n + 1);
+    for (int64_t i = 0; i <= c.n; ++i) crp[i] = (int32_t)C.rp[i];
+    if ((st = c.upload(&c.c_rp, crp.data(), c.n + 1))) return st;
+    if ((st = c.upload(&c.c_ci, C.ci.data(), C.nnz()))) return st;
+    if ((st = c.upload(&c.c_v, C.v.data(), C.nnz()))) return st;
+  }
   if (c.F.nc > 0) {
     const int64_t tot = c.F.nb * c.F.nblk;
     if ((st = c.upload(&c.fG, c.F.G.data(), tot * c.F.nb))) return st;
@@ -563,9 +769,10 @@ static int build_all(Ctx& c, const double* D) {
     fprintf(stderr, "amgf: n=%lld m=%lld nc=%lld levels=%d opcx=%.3f filter nb=%lld nblk=%lld cluster=%d staged=%d setup %.2fs\n",
             (long long)c.n, (long long)c.m, (long long)c.F.nc, nlev, in.op_complexity, (long long)c.F.nb,
             (long long)c.F.nblk, c.filter_cs, (int)c.filter_staged, in.t_setup_s);
+    fprintf(stderr, "  V-cycle precision: %s\n", c.mixed ? (c.k_bf16 ? "fp32 (fine K bf16)" : "fp32") : "fp64");
     for (int l = 0; l < nlev; ++l)
-      fprintf(stderr, "  level %d: rows %lld nnz %lld lanes %d%s\n", l, (long long)c.L[l].n, (long long)c.L[l].A.nnz,
-              c.L[l].A.K, c.L[l].A.bsr ? " (3x3 blocks)" : "");
+      fprintf(stderr, "  level %d: rows %lld nnz %lld lanes %d%s\n", l, (long long)c.L[l].n, (long long)c.H.A[l].nnz(),
+              c.mixed && l > 0 ? c.L[l].Af.K : c.L[l].A.K, c.L[l].A.bsr ? " (3x3 blocks)" : "");
   }
   CK(cudaDeviceSynchronize());
   return AMGF_OK;
@@ -615,6 +822,7 @@ int amgf_options_default(amgf_options* o) {
   o->maxit = 5000;
   o->use_graph = 1;
   o->verbose = 0;
+  o->precision = 0;
   return AMGF_OK;
 }
 
@@ -638,7 +846,8 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
   amgf_options opt;
   if (o) opt = *o; else amgf_options_default(&opt);
   if (opt.nu < 1 || opt.max_levels < 1 || opt.max_coarse < 1 || opt.num_functions < 1 || !(opt.rtol > 0.0) ||
-      opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2)
+      opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2 || opt.precision < 0 ||
+      opt.precision > 2)
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");
@@ -717,7 +926,7 @@ int amgf_vcycle(amgf_handle h, const double* r_dev, double* x_dev, void* stream)
   int st = join_begin(c, stream);
   if (st) return st;
   enqueue_scale_w0(c, r_dev);
-  enqueue_vcycle(c, r_dev, x_dev, nullptr, nullptr, nullptr);
+  enqueue_B(c, r_dev, x_dev, nullptr, nullptr, nullptr);
   return join_end(c, stream);
 }
 
@@ -858,8 +1067,9 @@ int amgf_export_contact_set(amgf_handle h, int64_t* ic) {
 
 int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* stream, double* ms, double* bytes) {
   if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
-  if (!h || !ms || !bytes || reps < 1 || warmup < 0 || which < 0 || which > 1)
+  if (!h || !ms || !bytes || reps < 1 || warmup < 0 || which < 0 || which > 2)
     return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  if (which == 2 && !h->c.mixed) return fail(AMGF_ERR_INVALID_ARG, "which = 2 needs a mixed-precision handle");
   Ctx& c = h->c;
   CK(cudaSetDevice(c.device));
   int st = join_begin(c, stream);
@@ -867,7 +1077,9 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
   DLevel& l0 = c.L[0];
   const double nnz = (double)l0.A.nnz, n = (double)l0.n;
   auto launch = [&]() {
-    if (which == 0) {
+    if (which == 2) {
+      launch_fine_mixed<M_POST>(c, l0.xf, l0.rhsf, l0.winvf, nullptr, nullptr, c.q, nullptr, nullptr);
+    } else if (which == 0) {
       CsrArgs a{};
       a.x = c.p; a.y = c.q;
       launch_csr<M_SPMV>(c, l0.A, a);
@@ -887,7 +1099,11 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
   *ms = t / reps;
   // values (8 B) + column indices (4 B) per nonzero, row pointers, and each vector read/written once
   const double vec_bytes = which == 0 ? 2.0 * 8.0 * n : 4.0 * 8.0 * n;
-  if (l0.A.bsr)  // 9 values + one block column index per block, block row pointers
+  if (which == 2) {  // K blocks (4 or 2 bytes per value + index), contact CSR, 3 FP32 reads + FP64 write
+    const double vb = c.k_bf16 ? 2.0 : 4.0;
+    *bytes = (double)c.k_nblocks * (9.0 * vb + 4.0) + (double)(c.k_nbrows + 1) * 8.0 + (n + 1) * 4.0 +
+             3.0 * 4.0 * n + 8.0 * n;
+  } else if (l0.A.bsr)  // 9 values + one block column index per block, block row pointers
     *bytes = (double)l0.A.nblocks * (9.0 * 8.0 + 4.0) + (double)(l0.A.nbrows + 1) * 8.0 + vec_bytes;
   else
     *bytes = nnz * 12.0 + (n + 1) * 8.0 + vec_bytes;

@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,24 +34,28 @@ constexpr int MAX_DOT_BLOCKS = 4096;
 //   RESID_W y = b - s, y2 = w2 * y     POST    y = x + w (b - s) [+ add]
 enum : int { M_SPMV = 0, M_SPMV_ADD = 1, M_RESID = 2, M_RESID_W = 3, M_POST = 4, M_SPMV_W = 5 };
 
-struct CsrArgs {
+template <typename T>
+struct CsrArgsT {
   const int64_t* __restrict__ rp;
   const int32_t* __restrict__ ci;
-  const double* __restrict__ v;
+  const T* __restrict__ v;
   int64_t nrows;
   const int64_t* __restrict__ rows;  // optional row indirection (output row = rows[i])
-  const double* x;      // gathered vector (unused by PRE)
-  const double* b;      // right-hand side (RESID, PRE, POST)
-  const double* winv;   // 1 / l1 of the rows (POST)
-  const double* w2;     // scaling written to y2 (RESID_W, SPMV_W)
-  const double* add;    // POST: optional vector added to the output
-  double* y;            // output
-  double* y2;           // RESID_W, SPMV_W: second output w2 * y
-  const double* dotv;   // DOT: partner vector of the output
+  const T* x;           // gathered vector
+  const T* b;           // right-hand side (RESID, POST)
+  const T* winv;        // 1 / l1 of the rows (POST)
+  const T* w2;          // scaling of the second output (RESID_W, SPMV_W)
+  const T* add;         // POST: optional vector added to the output
+  T* y;                 // output
+  T* y2;                // RESID_W, SPMV_W: second output w2 * y (may be null)
+  float* yf;            // optional FP32 copy of y (precision boundary into an FP32 V-cycle)
+  float* y2f;           // optional FP32 copy of w2 * y
+  const T* dotv;        // DOT: partner vector of the output
   double* partial;      // DOT: one partial per block
   double* result;       // DOT: final scalar
   unsigned* counter;    // DOT: arrival counter (zero between launches)
 };
+using CsrArgs = CsrArgsT<double>;
 
 struct PcgState {
   double rz;       // r_k^T z_k
@@ -59,10 +64,12 @@ struct PcgState {
   double pq;       // p^T A p
   double relres;   // sqrt(rz / rz0)
   double rtol;
+  double rz_cross; // r_{k+1}^T z_k (flexible PCG)
   int iter;
   int maxit;
   int done;
   int status;
+  int flexible;    // 1: beta = (r+^T z+ - r+^T z) / r^T z  (Polak-Ribiere; inexact preconditioner)
 };
 
 __device__ __forceinline__ double warp_sum(double s) {
@@ -105,8 +112,8 @@ __device__ __forceinline__ void grid_dot_finish(double local, double* partial, d
   }
 }
 
-template <int K, int MODE, bool DOT>
-__global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
+template <typename T, int K, int MODE, bool DOT>
+__global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T> a) {
   static_assert(K >= 1 && K <= 32 && (K & (K - 1)) == 0, "K must be a power of two <= 32");
   const int lane_w = threadIdx.x & 31;
   const int sub = lane_w & (K - 1);
@@ -117,7 +124,7 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
   for (int64_t base = warp_first; base < a.nrows; base += stride) {
     const int64_t i = base + lane_w / K;
     const bool valid = i < a.nrows;
-    double s = 0.0;
+    T s = T(0);
     if (valid) {
       const int64_t k1 = a.rp[i + 1];
       // batches of U entries per lane: all index/value loads of a batch are issued before
@@ -125,13 +132,13 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
       constexpr int U = 4;
       for (int64_t kb = a.rp[i] + sub; kb < k1; kb += U * K) {
         int32_t jj[U];
-        double vv[U];
+        T vv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int64_t k = kb + (int64_t)u * K;
           const bool ok = k < k1;
           jj[u] = ok ? __ldg(a.ci + k) : -1;
-          vv[u] = ok ? __ldg(a.v + k) : 0.0;
+          vv[u] = ok ? __ldg(a.v + k) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -142,14 +149,19 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgs a) {
     for (int off = K / 2; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off, K);
     if (valid && sub == 0) {
       const int64_t o = a.rows ? a.rows[i] : i;
-      double out;
+      T out;
       if (MODE == M_SPMV || MODE == M_SPMV_W) out = s;
       else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
       else if (MODE == M_RESID || MODE == M_RESID_W) out = a.b[o] - s;
       else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
       a.y[o] = out;
-      if (MODE == M_RESID_W || MODE == M_SPMV_W) a.y2[o] = a.w2[o] * out;
-      if (DOT) dacc += a.dotv[o] * out;
+      if (MODE == M_RESID_W || MODE == M_SPMV_W) {
+        const T w = a.w2[o] * out;
+        if (a.y2) a.y2[o] = w;
+        if (a.y2f) a.y2f[o] = (float)w;
+      }
+      if (a.yf) a.yf[o] = (float)out;
+      if (DOT) dacc += (double)a.dotv[o] * (double)out;
     }
   }
   if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
@@ -173,6 +185,8 @@ struct BsrArgs {
   const double* add;
   double* y;
   double* y2;
+  float* yf;
+  float* y2f;
   const double* dotv;
   double* partial;
   double* result;
@@ -212,28 +226,142 @@ __global__ void __launch_bounds__(TPB) bsr3_kernel(BsrArgs a) {
       }
     }
 #pragma unroll
-    for (int off = KB / 2; off > 0; off >>= 1) {
-      a0 += __shfl_down_sync(0xffffffffu, a0, off, KB);
-      a1 += __shfl_down_sync(0xffffffffu, a1, off, KB);
-      a2 += __shfl_down_sync(0xffffffffu, a2, off, KB);
+    for (int off = KB / 2; off > 0; off >>= 1) {  // butterfly: every lane of the group gets all three sums
+      a0 += __shfl_xor_sync(0xffffffffu, a0, off, KB);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, off, KB);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, off, KB);
     }
-    if (valid && sub == 0) {
+    if (valid && sub < 3) {  // lane c of the group finishes row 3I + c
+      const int c = sub;
+      const double s = c == 0 ? a0 : (c == 1 ? a1 : a2);
+      const int64_t o = 3 * I + c;
+      double out;
+      if (MODE == M_SPMV || MODE == M_SPMV_W) out = s;
+      else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
+      else if (MODE == M_RESID || MODE == M_RESID_W) out = a.b[o] - s;
+      else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
+      a.y[o] = out;
+      if (MODE == M_RESID_W || MODE == M_SPMV_W) {
+        const double w = a.w2[o] * out;
+        if (a.y2) a.y2[o] = w;
+        if (a.y2f) a.y2f[o] = (float)w;
+      }
+      if (a.yf) a.yf[o] = (float)out;
+      if (DOT) dacc += a.dotv[o] * out;
+    }
+  }
+  if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
+}
+
+// Fine level of the FP32 V-cycle: K in 3x3 node blocks with FP32 or BF16 values (same plane
+// layout as bsr3_kernel), FP32 vectors and accumulation, plus the contact term
+// J^T D J (entries up to D_max) in FP64 from a CSR over all rows (mostly empty), so that
+//   s_i = (K x)_i [FP32] + (J^T D J x)_i [FP64].
+//   RESID: y32 = b - s                        (pre-smoothing residual, FP32)
+//   POST : y64 = x + w (b - s) [+ add64]      (post-smoothing, written in FP64: the
+//          V-cycle's output crosses back into the FP64 PCG here)
+template <typename VT>
+struct Bsr3MixedArgs {
+  const int64_t* __restrict__ brp;
+  const int32_t* __restrict__ bci;
+  const VT* __restrict__ v;
+  int64_t nbrows;
+  const int32_t* __restrict__ crp;  // contact term rows (length n + 1)
+  const int32_t* __restrict__ cci;
+  const double* __restrict__ cv;
+  const float* x;
+  const float* b;
+  const float* winv;
+  const double* add;
+  float* y32;
+  double* y64;
+  const double* dotv;
+  double* partial;
+  double* result;
+  unsigned* counter;
+};
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename VT, int KB, int MODE, bool DOT>
+__global__ void __launch_bounds__(TPB) bsr3_mixed_kernel(Bsr3MixedArgs<VT> a) {
+  const int lane_w = threadIdx.x & 31;
+  const int sub = lane_w & (KB - 1);
+  const int64_t gid = ((int64_t)blockIdx.x * TPB + threadIdx.x) / KB;
+  const int64_t warp_first = gid - (lane_w / KB);
+  const int64_t stride = (int64_t)gridDim.x * (TPB / KB);
+  double dacc = 0.0;
+  for (int64_t base = warp_first; base < a.nbrows; base += stride) {
+    const int64_t I = base + lane_w / KB;
+    const bool valid = I < a.nbrows;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (valid) {
+      const int64_t s0 = a.brp[I];
+      const int64_t nbr = a.brp[I + 1] - s0;
+      const VT* vb = a.v + 9 * s0;
+      for (int64_t bb = sub; bb < nbr; bb += KB) {
+        const VT* p = vb + bb;
+        float m[9];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double s = c == 0 ? a0 : (c == 1 ? a1 : a2);
-        const int64_t o = 3 * I + c;
-        double out;
-        if (MODE == M_SPMV || MODE == M_SPMV_W) out = s;
-        else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
-        else if (MODE == M_RESID || MODE == M_RESID_W) out = a.b[o] - s;
-        else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
-        a.y[o] = out;
-        if (MODE == M_RESID_W || MODE == M_SPMV_W) a.y2[o] = a.w2[o] * out;
+        for (int q = 0; q < 9; ++q) m[q] = to_f32(p[q * nbr]);
+        const int64_t J = __ldg(a.bci + s0 + bb);
+        const float x0 = __ldg(a.x + 3 * J), x1 = __ldg(a.x + 3 * J + 1), x2 = __ldg(a.x + 3 * J + 2);
+        a0 += m[0] * x0 + m[1] * x1 + m[2] * x2;
+        a1 += m[3] * x0 + m[4] * x1 + m[5] * x2;
+        a2 += m[6] * x0 + m[7] * x1 + m[8] * x2;
+      }
+    }
+#pragma unroll
+    for (int off = KB / 2; off > 0; off >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, off, KB);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, off, KB);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, off, KB);
+    }
+    if (valid && sub < 3) {
+      const int64_t o = 3 * I + sub;
+      double s = (double)(sub == 0 ? a0 : (sub == 1 ? a1 : a2));
+      for (int32_t k = a.crp[o]; k < a.crp[o + 1]; ++k) s += a.cv[k] * (double)a.x[a.cci[k]];
+      if (MODE == M_RESID) {
+        a.y32[o] = (float)((double)a.b[o] - s);
+      } else {
+        double out = (double)a.x[o] + (double)a.winv[o] * ((double)a.b[o] - s);
+        if (a.add) out += a.add[o];
+        a.y64[o] = out;
         if (DOT) dacc += a.dotv[o] * out;
       }
     }
   }
   if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
+}
+
+// out = Ainv * r, single precision, one block (coarsest level of the FP32 V-cycle)
+__global__ void __launch_bounds__(TPB) dense_gemv_f32_kernel(int64_t n, const float* __restrict__ Ainv,
+                                                             const float* __restrict__ r, float* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    const float* row = Ainv + i * n;
+    float s = 0.f;
+    for (int64_t k = lane; k < n; k += 32) s += row[k] * r[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+// x_i += W_i * res_i in FP32 (extra sweeps when nu > 1)
+__global__ void axpy_w_f32_kernel(int64_t n, const float* __restrict__ winv, const float* __restrict__ res, float* x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += winv[i] * res[i];
+}
+
+// r32 = (float) r, x32 = (float)(W0 r): entry of an FP32 V-cycle from an FP64 vector
+__global__ void to_f32_scaled_kernel(int64_t n, const double* __restrict__ w, const double* __restrict__ r,
+                                     float* r32, float* x32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    r32[i] = (float)r[i];
+    x32[i] = (float)(w[i] * r[i]);
+  }
 }
 
 // y = W r elementwise (entry of a V-cycle whose rhs was not produced by a fused kernel)
@@ -408,10 +536,14 @@ __global__ void permute_kernel(int64_t n, const int64_t* __restrict__ scatter_to
 
 // ---------------- PCG ----------------
 
-// x += alpha p ; r -= alpha q with alpha = rz / pq (breakdown if pq <= 0); wr = W0 r (the
-// fine-level pre-smoothing iterate of the next V-cycle)
-__global__ void pcg_update_xr_kernel(PcgState* st, const double* __restrict__ p, const double* __restrict__ q,
-                                     double* x, double* r, const double* __restrict__ w0, double* wr, int64_t n) {
+// x += alpha p ; r -= alpha q with alpha = rz / pq (breakdown if pq <= 0).  Also writes the
+// entry of the next V-cycle: wr = W0 r (FP64 V-cycle) or r32 = r, wr32 = W0 r (FP32 V-cycle),
+// and with a flexible PCG the dot r_{k+1}^T z_k into st->rz_cross.
+__global__ void __launch_bounds__(TPB) pcg_update_xr_kernel(PcgState* st, const double* __restrict__ p,
+                                                            const double* __restrict__ q, double* x, double* r,
+                                                            const double* __restrict__ w0, double* wr, float* r32,
+                                                            float* wr32, const double* __restrict__ zold,
+                                                            double* partial, unsigned* counter, int64_t n) {
   if (st->done) return;
   const double pq = st->pq;
   if (!(pq > 0.0)) {
@@ -419,18 +551,23 @@ __global__ void pcg_update_xr_kernel(PcgState* st, const double* __restrict__ p,
     return;
   }
   const double alpha = st->rz / pq;
+  double dacc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
-    wr[i] = w0[i] * ri;
+    const double wri = w0[i] * ri;
+    if (wr) wr[i] = wri;
+    if (r32) { r32[i] = (float)ri; wr32[i] = (float)wri; }
+    if (zold) dacc += ri * zold[i];
   }
+  if (zold) grid_dot_finish(dacc, partial, &st->rz_cross, counter);
 }
 
 // p = z + beta p with beta = rz_new / rz
 __global__ void pcg_update_p_kernel(const PcgState* st, const double* __restrict__ z, double* p, int64_t n) {
   if (st->done) return;
-  const double beta = st->rz_new / st->rz;
+  const double beta = st->flexible ? (st->rz_new - st->rz_cross) / st->rz : st->rz_new / st->rz;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
 }
@@ -453,8 +590,10 @@ __global__ void pcg_finalize_kernel(PcgState* st, cudaGraphConditionalHandle con
 }
 
 // After r0 = b - A x0 and z0 = M r0 (rz_new = r0^T z0): initialise the scalars.
-__global__ void pcg_init_kernel(PcgState* st, int maxit, double rtol) {
+__global__ void pcg_init_kernel(PcgState* st, int maxit, double rtol, int flexible) {
   const double rz = st->rz_new;
+  st->flexible = flexible;
+  st->rz_cross = 0.0;
   st->rz = rz;
   st->rz0 = rz;
   st->iter = 0;

@@ -1,0 +1,103 @@
+"""Mixed precision (FP32 V-cycle, optional BF16 fine-level K) inside the FP64 flexible PCG.
+
+The oracle is FP64 throughout; each mixed result is checked against it:
+  - V-cycle: ||B32 r - B r|| / ||B r|| is of the order of the FP32 unit roundoff times the
+    hierarchy's amplification: asserted <= 1e-4 (FP32) and <= 5e-2 (BF16 K: 2^-9 relative
+    perturbation of every fine-level value).
+  - PCG: converges to rtol 1e-8 and the solution's A-norm distance to the oracle's is at most
+    4 rtol sqrt(kappa(MA)) (each solve's A-norm error is bounded by rtol sqrt(kappa); the
+    factor 2 margin covers the FP32 preconditioner's spectrum differing slightly from M's).
+"""
+import numpy as np
+import pytest
+
+import contactgen as cg
+import oracle
+from oracle.lanczos import kappa_estimate
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "tiny": dict(nx=8, ny=8, nz=4, d_lo=-2, d_hi=4),
+    "n16": dict(nx=16, ny=12, nz=7, d_lo=-2, d_hi=8),
+    "n24": dict(nx=24, ny=24, nz=12, d_lo=-2, d_hi=10),
+}
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, np.float64)).cuda()
+
+
+def a_norm(S, v):
+    return float(np.sqrt(v @ (S @ v)))
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    p = cg.make_problem(None, seed=5, **CASES[request.param])
+    return request.param, p, oracle.Oracle(p.K, p.J, p.D)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-4), (2, 5e-2)])
+def test_mixed_vcycle_close_to_fp64(case, precision, tol):
+    import paper_2505_18576_gb300 as m
+    name, p, o = case
+    s = m.Solver(p.K, p.J, p.D, precision=precision)
+    r = np.random.default_rng(1).standard_normal(p.n)
+    x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(r), x)
+    torch.cuda.synchronize()
+    xo = o.vcycle(r)
+    err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+    print(f"{name} precision {precision}: V-cycle rel diff {err:.2e}")
+    assert err <= tol
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_pcg_against_fp64_oracle(case, precision):
+    import paper_2505_18576_gb300 as m
+    name, p, o = case
+    xo, ko, sto, al, be, _ = o.pcg(p.b, tol=1e-8)
+    kap, _, _ = kappa_estimate(al, be)
+    s = m.Solver(p.K, p.J, p.D, precision=precision)
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(dev(p.b), x)
+    torch.cuda.synchronize()
+    S = o.S()
+    d = x.cpu().numpy() - xo
+    ea = a_norm(S, d) / a_norm(S, xo)
+    print(f"{name} precision {precision}: iters {st.iters} (fp64 oracle {ko}), A-norm diff {ea:.2e} "
+          f"(bound {4e-8 * np.sqrt(kap):.2e})")
+    assert st.status == 0 and st.converged == 1
+    assert st.iters <= 2 * ko + 5
+    assert ea <= 4e-8 * np.sqrt(kap)
+    s.close()
+
+
+def test_mixed_apply_close_to_fp64(case):
+    import paper_2505_18576_gb300 as m
+    name, p, o = case
+    s = m.Solver(p.K, p.J, p.D, precision=1)
+    r = np.random.default_rng(2).standard_normal(p.n)
+    z = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.apply(dev(r), z)
+    torch.cuda.synchronize()
+    zo = o.apply(r)
+    err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
+    print(f"{name}: mixed apply rel diff {err:.2e}")
+    assert err <= 1e-3
+    s.close()
+
+
+def test_mixed_deterministic(case):
+    import paper_2505_18576_gb300 as m
+    name, p, o = case
+    s = m.Solver(p.K, p.J, p.D, precision=1)
+    x1 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    s1 = s.pcg_solve(dev(p.b), x1)
+    s2 = s.pcg_solve(dev(p.b), x2)
+    assert s1.iters == s2.iters and torch.equal(x1, x2)
+    s.close()

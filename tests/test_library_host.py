@@ -106,6 +106,9 @@ def test_invalid_inputs(tiny):
     with pytest.raises(amgf.AmgfError) as e:
         amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, nu=0)
     assert e.value.status == 1
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, precision=3)
+    assert e.value.status == 1
 
 
 def test_update_D_host(tiny):

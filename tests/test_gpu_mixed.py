@@ -5,8 +5,10 @@ The oracle is FP64 throughout; each mixed result is checked against it:
     hierarchy's amplification: asserted <= 1e-4 (FP32) and <= 5e-2 (BF16 K: 2^-9 relative
     perturbation of every fine-level value).
   - PCG: converges to rtol 1e-8 and the solution's A-norm distance to the oracle's is at most
-    4 rtol sqrt(kappa(MA)) (each solve's A-norm error is bounded by rtol sqrt(kappa); the
-    factor 2 margin covers the FP32 preconditioner's spectrum differing slightly from M's).
+    max(4 rtol sqrt(kappa(MA)), 10 f): each solve's A-norm error is bounded by rtol sqrt(kappa)
+    (factor 2 margin for the FP32 preconditioner's spectrum), and f is the FP64 rounding floor
+    measured on the oracle itself (A-norm spread of two solves started 1e-10 |b| apart), which
+    grows with D_max (3e-8 at 1e8, 8e-7 at 1e10).
 """
 import numpy as np
 import pytest
@@ -61,18 +63,21 @@ def test_mixed_pcg_against_fp64_oracle(case, precision):
     name, p, o = case
     xo, ko, sto, al, be, _ = o.pcg(p.b, tol=1e-8)
     kap, _, _ = kappa_estimate(al, be)
+    S = o.S()
+    x2, *_ = o.pcg(p.b, x0=1e-10 * np.abs(p.b), tol=1e-8)
+    floor = a_norm(S, x2 - xo) / a_norm(S, xo)
+    bound = max(4e-8 * np.sqrt(kap), 10 * floor)
     s = m.Solver(p.K, p.J, p.D, precision=precision)
     x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
     st = s.pcg_solve(dev(p.b), x)
     torch.cuda.synchronize()
-    S = o.S()
     d = x.cpu().numpy() - xo
     ea = a_norm(S, d) / a_norm(S, xo)
     print(f"{name} precision {precision}: iters {st.iters} (fp64 oracle {ko}), A-norm diff {ea:.2e} "
-          f"(bound {4e-8 * np.sqrt(kap):.2e})")
+          f"(bound {bound:.2e}, floor {floor:.2e})")
     assert st.status == 0 and st.converged == 1
     assert st.iters <= 2 * ko + 5
-    assert ea <= 4e-8 * np.sqrt(kap)
+    assert ea <= bound
     s.close()
 
 

@@ -44,7 +44,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("strength_theta", ctypes.c_double), ("max_coarse", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("num_functions", ctypes.c_int),
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int),
-                ("contact_components", ctypes.c_int)]
+                ("contact_components", ctypes.c_int), ("build_amg", ctypes.c_int)]
 
 
 def _load():
@@ -74,9 +74,11 @@ def _load():
     lib.orc_mat_shape.restype = i32
     lib.orc_mat_get.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.orc_mat_get.restype = i32
-    for f in ("orc_get_cf", "orc_get_l1", "orc_get_func"):
+    for f in ("orc_get_cf", "orc_get_l1", "orc_get_func", "orc_get_theta"):
         getattr(lib, f).argtypes = [vp, i32, vp]
         getattr(lib, f).restype = i32
+    lib.orc_set_mlp.argtypes = [vp, vp, i64]
+    lib.orc_set_mlp.restype = i32
     _lib = lib
     return lib
 
@@ -217,6 +219,23 @@ class Oracle:
     def l1(self, l):
         out = np.empty(self.A(l).shape[0])
         self._lib.orc_get_l1(self._h, l, _p(out)); return out
+
+    def set_mlp(self, w):
+        """Learned smoother weights (1313 values; None clears them: theta = 1)."""
+        if w is None:
+            self._lib.orc_set_mlp(self._h, None, 0)
+            return
+        w = np.ascontiguousarray(w, np.float64)
+        self._mlp_w = w
+        st = self._lib.orc_set_mlp(self._h, _p(w), len(w))
+        if st:
+            raise OracleError(st, "set_mlp")
+
+    def theta(self, l):
+        out = np.empty(self.A(l).shape[0])
+        if self._lib.orc_get_theta(self._h, l, _p(out)):
+            raise IndexError(l)
+        return out
 
     def func(self, l):
         out = np.empty(self.A(l).shape[0], np.int32)

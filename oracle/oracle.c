@@ -67,6 +67,7 @@ typedef struct {
   int nu;                /* smoothing sweeps down and up (1) */
   int filter;            /* 0: M = B (AMG-PCG); 1: AMGF */
   int contact_components;/* 0: I_c = nonzero columns of J; 1: all 3 DOFs of those nodes; 2: all DOFs */
+  int build_amg;         /* 1: full setup; 0: assemble A only (for A x on large problems) */
 } orc_opts;
 
 typedef struct {
@@ -79,6 +80,7 @@ typedef struct {
   int8_t* cf[32]; /* 1 = C, 0 = F */
   double* Lc;   /* dense Cholesky factor of coarsest A (row-major, lower) */
   int64_t nc_dense;
+  double* theta[32]; /* per-row smoother weights (NULL: theta = 1) */
 } orc_amg;
 
 typedef struct {
@@ -95,6 +97,8 @@ typedef struct {
   /* work */
   double* w[8];
   char err[256];
+  double* dcontact;  /* diagonal of J^T D J (length n) */
+  int8_t* ccontact;  /* 1 if the DOF is a nonzero column of J */
 } orc_t;
 
 static void* xmalloc(size_t n) {
@@ -479,12 +483,13 @@ static void vcycle(orc_t* h, int l, const double* r, double* x) {
   int64_t n = A->nrows;
   if (l == g->nlev - 1) { dense_chol_solve(g->Lc, n, r, x); return; }
   const double* l1 = g->l1[l];
+  const double* th = g->theta[l];
   double* res = xmalloc(n * sizeof(double));
-  /* pre-smoothing from x = 0 */
-  for (int64_t i = 0; i < n; ++i) x[i] = r[i] / l1[i];
+  /* pre-smoothing from x = 0: x = W r, W = diag(theta / l1) (theta = 1 without weights) */
+  for (int64_t i = 0; i < n; ++i) x[i] = th ? (th[i] / l1[i]) * r[i] : r[i] / l1[i];
   for (int s = 1; s < h->o.nu; ++s) {
     csr_resid(A, r, x, res);
-    for (int64_t i = 0; i < n; ++i) x[i] += res[i] / l1[i];
+    for (int64_t i = 0; i < n; ++i) x[i] += th ? (th[i] / l1[i]) * res[i] : res[i] / l1[i];
   }
   /* coarse-grid correction */
   csr_resid(A, r, x, res);
@@ -496,10 +501,10 @@ static void vcycle(orc_t* h, int l, const double* r, double* x) {
   double* pe = xmalloc(n * sizeof(double));
   csr_mv(&g->P[l], ec, pe);
   for (int64_t i = 0; i < n; ++i) x[i] += pe[i];
-  /* post-smoothing */
+  /* post-smoothing (same W as before the coarse correction, so B stays symmetric) */
   for (int s = 0; s < h->o.nu; ++s) {
     csr_resid(A, r, x, res);
-    for (int64_t i = 0; i < n; ++i) x[i] += res[i] / l1[i];
+    for (int64_t i = 0; i < n; ++i) x[i] += th ? (th[i] / l1[i]) * res[i] : res[i] / l1[i];
   }
   free(res); free(rc); free(ec); free(pe);
 }
@@ -662,6 +667,7 @@ void orc_opts_default(orc_opts* o) {
   o->nu = 1;
   o->filter = 1;
   o->contact_components = 0;
+  o->build_amg = 1;
 }
 
 const char* orc_error(orc_t* h) { return h ? h->err : "null handle"; }
@@ -681,6 +687,14 @@ int orc_create(int64_t n,
     else if (!(D[r] > 0.0)) { free(h); return ORC_NOT_SPD; }
   ocsr K = {n, n, (int64_t*)Krp, (int32_t*)Kci, (double*)Kv};
   ocsr J = {m, n, (int64_t*)Jrp, (int32_t*)Jci, (double*)Jv};
+  /* per-DOF contact data for the learned smoother's features: (J^T D J)_aa and the flag */
+  h->dcontact = xcalloc(n, sizeof(double));
+  h->ccontact = xcalloc(n, 1);
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t k = Jrp[r]; k < Jrp[r + 1]; ++k) {
+      h->dcontact[Jci[k]] += Jv[k] * (D[r] * Jv[k]);
+      if (Jv[k] != 0.0) h->ccontact[Jci[k]] = 1;
+    }
   if (m > 0) assemble_S(&K, &J, D, &h->S);
   else {
     int64_t nnz = Krp[n];
@@ -688,6 +702,11 @@ int orc_create(int64_t n,
     h->S.rp = xmalloc((n + 1) * sizeof(int64_t)); memcpy(h->S.rp, Krp, (n + 1) * sizeof(int64_t));
     h->S.ci = xmalloc(nnz * sizeof(int32_t)); memcpy(h->S.ci, Kci, nnz * sizeof(int32_t));
     h->S.v = xmalloc(nnz * sizeof(double)); memcpy(h->S.v, Kv, nnz * sizeof(double));
+  }
+  if (!h->o.build_amg) {
+    for (int i = 0; i < 8; ++i) h->w[i] = xmalloc(n * sizeof(double));
+    *out = h;
+    return ORC_OK;
   }
   int st = amg_setup(h);
   if (st != ORC_OK) { *out = h; return st; }
@@ -706,8 +725,9 @@ void orc_free(orc_t* h) {
   csr_free(&h->S);
   for (int l = 0; l < 32; ++l) {
     csr_free(&h->amg.A[l]); csr_free(&h->amg.P[l]); csr_free(&h->amg.R[l]);
-    free(h->amg.l1[l]); free(h->amg.func[l]); free(h->amg.cf[l]);
+    free(h->amg.l1[l]); free(h->amg.func[l]); free(h->amg.cf[l]); free(h->amg.theta[l]);
   }
+  free(h->dcontact); free(h->ccontact);
   free(h->amg.Lc); free(h->Ic); free(h->perm); free(h->Lb);
   for (int i = 0; i < 8; ++i) free(h->w[i]);
   free(h);
@@ -796,6 +816,89 @@ int orc_pcg(orc_t* h, const double* b, double* x, double tol, int maxit,
 done:
   free(r); free(z); free(p); free(q);
   return status;
+}
+
+/* ---------------- learned smoother weights (test infrastructure) ----------------
+ * Per-row damping theta_i of the l1-Jacobi smoother, W = diag(theta / l1), predicted by a
+ * small MLP from local features; theta = 0.3 + 0.9 sigmoid(o) keeps theta in [0.3, 1.2]
+ * (< 2, so the l1 smoother stays convergent and B stays SPD).  Features of row i on level l:
+ *   f0 = log10(a_ii) / 10, f1 = log10(l1_i) / 10, f2 = a_ii / l1_i, f3 = contact flag,
+ *   f4 = log10(1 + d_i) / 10 with d = diag(J^T D J) on level 0, f5 = l / (nlev - 1);
+ * the flag and d of a coarse row are those of the fine C point it comes from.
+ * Weights (1313): W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3. */
+#define MLP_NW 1313
+
+static void mlp_features(orc_t* h, int l, const double* dl, const int8_t* cl, double* f /* n_l x 6 */) {
+  const ocsr* A = &h->amg.A[l];
+  int nlev = h->amg.nlev;
+  for (int64_t i = 0; i < A->nrows; ++i) {
+    double aii = 0.0;
+    for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k)
+      if (A->ci[k] == i) aii = A->v[k];
+    double l1 = h->amg.l1[l][i];
+    f[6 * i + 0] = log10(aii) / 10.0;
+    f[6 * i + 1] = log10(l1) / 10.0;
+    f[6 * i + 2] = aii / l1;
+    f[6 * i + 3] = cl[i] ? 1.0 : 0.0;
+    f[6 * i + 4] = log10(1.0 + dl[i]) / 10.0;
+    f[6 * i + 5] = nlev > 1 ? (double)l / (double)(nlev - 1) : 0.0;
+  }
+}
+
+static double mlp_theta(const double* w, const double* f) {
+  const double* W1 = w;          /* [32][6] */
+  const double* b1 = w + 192;
+  const double* W2 = w + 224;    /* [32][32] */
+  const double* b2 = w + 1248;
+  const double* w3 = w + 1280;
+  const double b3 = w[1312];
+  double h1[32], h2[32];
+  for (int j = 0; j < 32; ++j) {
+    double s = b1[j];
+    for (int k = 0; k < 6; ++k) s += W1[6 * j + k] * f[k];
+    h1[j] = s > 0.0 ? s : 0.0;
+  }
+  for (int j = 0; j < 32; ++j) {
+    double s = b2[j];
+    for (int k = 0; k < 32; ++k) s += W2[32 * j + k] * h1[k];
+    h2[j] = s > 0.0 ? s : 0.0;
+  }
+  double o = b3;
+  for (int k = 0; k < 32; ++k) o += w3[k] * h2[k];
+  return 0.3 + 0.9 / (1.0 + exp(-o));
+}
+
+/* Set (w != NULL) or clear (w == NULL) the learned weights of every smoothed level. */
+int orc_set_mlp(orc_t* h, const double* w, int64_t nw) {
+  orc_amg* g = &h->amg;
+  for (int l = 0; l < 32; ++l) { free(g->theta[l]); g->theta[l] = NULL; }
+  if (!w) return ORC_OK;
+  if (nw != MLP_NW) return ORC_INVALID;
+  int64_t n0 = g->A[0].nrows;
+  double* dl = xmalloc(n0 * sizeof(double));
+  int8_t* cl = xmalloc(n0);
+  memcpy(dl, h->dcontact, n0 * sizeof(double));
+  memcpy(cl, h->ccontact, n0);
+  for (int l = 0; l + 1 < g->nlev; ++l) {
+    int64_t n = g->A[l].nrows;
+    double* f = xmalloc(6 * n * sizeof(double));
+    mlp_features(h, l, dl, cl, f);
+    g->theta[l] = xmalloc(n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) g->theta[l][i] = mlp_theta(w, f + 6 * i);
+    free(f);
+    /* inherit d and the flag to the coarse level through the C points */
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (g->cf[l][i]) { dl[c] = dl[i]; cl[c] = cl[i]; c++; }
+  }
+  free(dl); free(cl);
+  return ORC_OK;
+}
+
+int orc_get_theta(orc_t* h, int l, double* out) {
+  if (l < 0 || l >= h->amg.nlev - 1 || !h->amg.theta[l]) return ORC_INVALID;
+  memcpy(out, h->amg.theta[l], h->amg.A[l].nrows * sizeof(double));
+  return ORC_OK;
 }
 
 /* ---------------- introspection (tests) ---------------- */

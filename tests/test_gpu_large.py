@@ -1,0 +1,65 @@
+"""Full-form configuration (c160: two blocks of 160x160x80 Q1 elements, n = 12,442,080,
+m = 25,921, D log-uniform in [1e-2, 1e12]) on the GPU, checked against the oracle where it can
+compute at this size (the oracle assembles A = K + J^T D J; its AMG setup is not run here):
+
+  - A x: every row within the dot-product forward error bound 2 gamma_k (|A||x|)_i.
+  - PCG solutions (FP64, and FP32 V-cycle with BF16 fine-level K): converged to rtol 1e-8, and
+    the Galerkin residual |x^T (b - A x)| / (b^T x) (A from the oracle) below 1e-5: for a CG
+    iterate this equals ||e||_A ||x||_A-weighted and is bounded by rtol sqrt(kappa(MA))
+    (~1e-7 here) plus the FP64 floor of A x with entries up to 1e12.
+  - the two solutions agree in the oracle's A-norm within 1e-5.
+"""
+import numpy as np
+import pytest
+
+import contactgen as cg
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def c160():
+    p = cg.make_problem("c160", seed=0)
+    o = oracle.Oracle(p.K, p.J, p.D, build_amg=0)
+    yield p, o
+    o.close()
+
+
+def test_c160_matvec_and_solves(c160):
+    import paper_2505_18576_gb300 as m
+    p, o = c160
+    n = p.n
+    b = torch.from_numpy(p.b).cuda()
+    xs = {}
+    for prec in (0, 2):
+        s = m.Solver(p.K, p.J, p.D, precision=prec)
+        if prec == 0:
+            xr = np.random.default_rng(3).standard_normal(n)
+            y = torch.empty(n, dtype=torch.float64, device="cuda")
+            s.matvec(torch.from_numpy(xr).cuda(), y)
+            torch.cuda.synchronize()
+            yo = o.S_apply(xr)
+            S = o.S()
+            k = np.diff(S.indptr)
+            bound = 2 * k * EPS / (1 - k * EPS) * (abs(S) @ np.abs(xr))
+            assert np.all(np.abs(y.cpu().numpy() - yo) <= bound + 1e-300)
+            del S
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = s.pcg_solve(b, x)
+        torch.cuda.synchronize()
+        xh = x.cpu().numpy()
+        r = p.b - o.S_apply(xh)
+        gal = abs(xh @ r) / abs(p.b @ xh)
+        print(f"c160 precision {prec}: iters {st.iters} relres {st.rel_res_precond:.2e} t {st.t_solve_s:.3f}s "
+              f"galerkin residual {gal:.2e}")
+        assert st.status == 0 and st.converged == 1
+        assert gal <= 1e-5
+        xs[prec] = xh
+        s.close()
+    d = xs[0] - xs[2]
+    ea = np.sqrt(abs(d @ o.S_apply(d))) / np.sqrt(xs[0] @ o.S_apply(xs[0]))
+    print(f"c160 fp64 vs mixed A-norm diff {ea:.2e}")
+    assert ea <= 1e-5

@@ -84,6 +84,8 @@ typedef struct {
   double rz0;             /* r0^T z0 */
   double t_solve_s;       /* device time of the solve (CUDA events) */
   int64_t kernel_launches;/* this library's kernels executed by the solve */
+  int mlp_fallback;       /* 1: the learned weights missed the stop test and the solve was redone
+                             with theta = 1 (the plain l1-Jacobi smoother) */
 } amgf_stats;
 
 typedef struct {
@@ -159,6 +161,28 @@ int amgf_pcg_solve(amgf_handle h, const double* b_dev, double* x_dev, amgf_stats
 /* Same as amgf_pcg_solve with host arrays (length n): copies b and x0 to the device,
  * solves, copies x back.  Blocking. */
 int amgf_pcg_solve_host(amgf_handle h, const double* b_host, double* x_host, amgf_stats* st);
+
+/* Learned smoother (not in the paper).  Every smoothed level's l1-Jacobi step is scaled
+ * per row, W_i = theta_i / l1_i, with theta_i = 0.3 + 0.9 sigmoid(MLP(f_i)), an MLP
+ * 6 -> 32 -> 32 -> 1 (ReLU) evaluated in FP32 on the GPU from the row's features f_i =
+ * (log10(a_ii)/10, log10(l1_i)/10, a_ii/l1_i, contact flag, log10(1 + d_i)/10, l/(nlev-1)),
+ * d = diag(J^T D J) on the fine level (a coarse row inherits flag and d from its fine C point).
+ * theta in [0.3, 1.2] < 2 keeps the smoother convergent and B, M SPD.
+ * weights: host array of 1313 floats laid out W1[32][6], b1[32], W2[32][32], b2[32],
+ * w3[32], b3; NULL restores theta = 1.  The weights stay active across amgf_update_D.
+ * With active weights, a PCG solve that misses its stop test is redone with theta = 1
+ * (amgf_stats.mlp_fallback = 1). */
+int amgf_set_mlp(amgf_handle h, const float* weights, int64_t nw);
+
+/* `iters` Adam steps (lr, beta 0.9/0.999) on the MLP weights for this handle's hierarchy:
+ * loss = mean over smoothed levels of ||(I - A_l W_l) r_l||^2 / ||r_l||^2 with r_l uniform in
+ * (-1, 1) from SplitMix64 counters derived from `seed` and the step number.  params, adam_m,
+ * adam_v (1313 floats each) and *adam_step are read and updated (host memory); loss (host,
+ * length iters, may be NULL) receives the loss before each step.  Forward, backward and
+ * update run in this library's kernels.  Needs an FP64 handle (precision 0) with >= 2 levels.
+ * The active smoother weights (amgf_set_mlp) are left unchanged. */
+int amgf_mlp_train(amgf_handle h, float* params, float* adam_m, float* adam_v, int64_t* adam_step,
+                   int iters, float lr, uint64_t seed, float* loss);
 
 /* Hierarchy and sizes. */
 int amgf_get_info(amgf_handle h, amgf_info* info);

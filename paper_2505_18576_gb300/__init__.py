@@ -27,7 +27,7 @@ EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_updat
             "amgf_filter_solve", "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host",
             "amgf_get_info",
             "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
-            "amgf_last_error"]
+            "amgf_last_error", "amgf_set_mlp", "amgf_mlp_train"]
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "NOT_SPD", 4: "BREAKDOWN", 5: "NOT_CONVERGED",
           6: "CUDA", 7: "OOM"}
@@ -55,7 +55,8 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("rel_res_precond", ctypes.c_double), ("rz0", ctypes.c_double),
-                ("t_solve_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("t_solve_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("mlp_fallback", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -97,6 +98,8 @@ def load_library(build_if_missing: bool = True):
         "amgf_export_contact_set": [vp, vp],
         "amgf_time_kernel": [vp, i32, i32, i32, vp, vp, vp],
         "amgf_destroy": [vp],
+        "amgf_set_mlp": [vp, vp, i64],
+        "amgf_mlp_train": [vp, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_uint64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -264,6 +267,27 @@ def amgf_time_kernel(h, which: int, warmup: int, reps: int, stream=None):
     return ms.value, by.value
 
 
+def amgf_set_mlp(h, weights):
+    """Activate learned smoother weights (1313 floats) or restore theta = 1 (None)."""
+    if weights is None:
+        _check(load_library().amgf_set_mlp(h, None, 0))
+        return
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(load_library().amgf_set_mlp(h, _ptr(w), len(w)))
+
+
+def amgf_mlp_train(h, params, adam_m, adam_v, adam_step, iters: int, lr: float, seed: int):
+    """Adam steps on the smoother MLP for this handle's hierarchy; updates the float32 arrays in
+    place and returns (new adam_step, losses)."""
+    for a in (params, adam_m, adam_v):
+        assert a.dtype == np.float32 and a.flags.c_contiguous and len(a) == 1313
+    step = ctypes.c_int64(adam_step)
+    loss = np.zeros(max(iters, 1), np.float32)
+    _check(load_library().amgf_mlp_train(h, _ptr(params), _ptr(adam_m), _ptr(adam_v), ctypes.byref(step), iters,
+                                         lr, seed, _ptr(loss)))
+    return step.value, loss[:iters]
+
+
 def amgf_destroy(h):
     if h:
         load_library().amgf_destroy(h)
@@ -319,6 +343,9 @@ class Solver:
 
     def contact_set(self):
         return amgf_export_contact_set(self.h, self.nc)
+
+    def set_mlp(self, weights):
+        amgf_set_mlp(self.h, weights)
 
     def time_kernel(self, which: int, warmup: int = 3, reps: int = 20, stream=None):
         return amgf_time_kernel(self.h, which, warmup, reps, stream)

@@ -105,6 +105,15 @@ struct Ctx {
   void* k_v = nullptr;
   int32_t *c_rp = nullptr, *c_ci = nullptr;
   double* c_v = nullptr;
+  // learned smoother: per-level features (6 FP32 per row) and l1 sums, weights, training scratch
+  std::vector<float*> feat_d;
+  std::vector<double*> l1_d;
+  std::vector<float> mlp_w_host;  // active weights (empty: theta = 1)
+  float* mlp_w = nullptr;
+  float *mlp_m = nullptr, *mlp_v = nullptr, *mlp_g = nullptr, *mlp_part = nullptr, *mlp_loss = nullptr;
+  double *mlp_tw = nullptr, *mlp_ee = nullptr, *mlp_rr = nullptr;
+  int64_t mlp_part_blocks = 0;
+  int mlp_loss_cap = 0;
   double *fG = nullptr, *fGT = nullptr, *fDinv = nullptr, *fy = nullptr, *fz = nullptr, *fw = nullptr, *fv = nullptr;
   int64_t* fgidx = nullptr;
   int64_t* ficidx = nullptr;  // factor position -> index into I_c
@@ -139,6 +148,12 @@ struct Ctx {
     for (void* a : allocs) cudaFree(a);
     allocs.clear();
     L.clear();
+    feat_d.clear();
+    l1_d.clear();
+    mlp_w = mlp_m = mlp_v = mlp_g = mlp_part = mlp_loss = nullptr;
+    mlp_tw = mlp_ee = mlp_rr = nullptr;
+    mlp_part_blocks = 0;
+    mlp_loss_cap = 0;
   }
   void release() {
     release_device();
@@ -543,6 +558,85 @@ static int build_graph(Ctx& c) {
   return AMGF_OK;
 }
 
+// W_l = theta / l1 on every smoothed level from the active weights (theta = 1 without them)
+static int apply_smoother_weights(Ctx& c, bool plain) {
+  const bool use = !plain && !c.mlp_w_host.empty();
+  if (use) CK(cudaMemcpyAsync(c.mlp_w, c.mlp_w_host.data(), MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
+  for (int l = 0; l + 1 < (int)c.L.size(); ++l) {
+    DLevel& lv = c.L[l];
+    mlp_infer_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, c.feat_d[l], c.mlp_w, use ? 0 : 1, c.l1_d[l], lv.winv,
+                                                        lv.winvf);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c.s));
+  return AMGF_OK;
+}
+
+// Adam steps on the smoothing loss sum_l ||(I - A_l W_l(theta)) r_l||^2 / ||r_l||^2 (averaged over
+// the smoothed levels), r_l uniform(-1, 1) from the counter-based generator.
+static int mlp_train_impl(Ctx& c, float* params, float* adam_m, float* adam_v, int64_t* adam_step, int iters,
+                          float lr, uint64_t seed, float* loss) {
+  const int nsm = (int)c.L.size() - 1;
+  if (nsm < 1) return fail(AMGF_ERR_INVALID_ARG, "training needs at least two levels");
+  int st;
+  if (!c.mlp_m) {
+    int64_t maxn = 0;
+    for (int l = 0; l < nsm; ++l) maxn = std::max<int64_t>(maxn, c.L[l].n);
+    c.mlp_part_blocks = (maxn + TPB - 1) / TPB;
+    if ((st = c.alloc(&c.mlp_m, MLP_NW))) return st;
+    if ((st = c.alloc(&c.mlp_v, MLP_NW))) return st;
+    if ((st = c.alloc(&c.mlp_g, MLP_NW))) return st;
+    if ((st = c.alloc(&c.mlp_part, c.mlp_part_blocks * MLP_NW))) return st;
+    if ((st = c.alloc(&c.mlp_tw, maxn))) return st;
+    if ((st = c.alloc(&c.mlp_ee, 32))) return st;
+    if ((st = c.alloc(&c.mlp_rr, 32))) return st;
+    CK(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
+  }
+  if (iters > c.mlp_loss_cap) {
+    if ((st = c.alloc(&c.mlp_loss, iters))) return st;
+    c.mlp_loss_cap = iters;
+  }
+  CK(cudaMemcpyAsync(c.mlp_w, params, MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
+  CK(cudaMemcpyAsync(c.mlp_m, adam_m, MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
+  CK(cudaMemcpyAsync(c.mlp_v, adam_v, MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
+  const float scale = 1.0f / (float)nsm;
+  int64_t t = *adam_step;
+  for (int it = 0; it < iters; ++it) {
+    for (int l = 0; l < nsm; ++l) {
+      DLevel& lv = c.L[l];
+      const int g = vec_grid(c, lv.n);
+      const uint64_t sd = seed ^ (0x632BE59BD9B4E019ull * (uint64_t)(t + 1)) ^ ((uint64_t)l << 56);
+      rand_uniform_kernel<<<g, TPB, 0, c.s>>>(lv.n, sd, lv.rhs);                       // r
+      dot_kernel<<<g, TPB, 0, c.s>>>(lv.n, lv.rhs, lv.rhs, c.partial, c.mlp_rr + l, c.counter);
+      mlp_infer_kernel<<<g, TPB, 0, c.s>>>(lv.n, c.feat_d[l], c.mlp_w, 0, c.l1_d[l], c.mlp_tw, nullptr);
+      scale_kernel<<<g, TPB, 0, c.s>>>(lv.n, c.mlp_tw, lv.rhs, lv.x);                    // x = W r
+      CsrArgs e{};
+      e.x = lv.x; e.b = lv.rhs; e.y = lv.res;
+      launch_csr<M_RESID>(c, lv.A, e, lv.res, c.mlp_ee + l);                            // e = r - A x
+      CsrArgs ae{};
+      ae.x = lv.res; ae.y = lv.out;
+      launch_csr<M_SPMV>(c, lv.A, ae);                                                   // A e
+      const int nb = (int)((lv.n + TPB - 1) / TPB);
+      mlp_backward_kernel<<<nb, TPB, MLP_SMEM, c.s>>>(lv.n, c.feat_d[l], c.mlp_w, lv.rhs, c.l1_d[l], lv.out,
+                                                      c.mlp_rr + l, scale, c.mlp_part);
+      mlp_grad_reduce_kernel<<<(MLP_NW + TPB - 1) / TPB, TPB, 0, c.s>>>(nb, c.mlp_part, c.mlp_g, l > 0 ? 1 : 0);
+    }
+    mlp_loss_kernel<<<1, 1, 0, c.s>>>(nsm, c.mlp_ee, c.mlp_rr, scale, c.mlp_loss + it);
+    ++t;
+    mlp_adam_kernel<<<(MLP_NW + TPB - 1) / TPB, TPB, 0, c.s>>>(c.mlp_w, c.mlp_m, c.mlp_v, c.mlp_g, lr, 0.9f, 0.999f,
+                                                              1e-8f, (float)t);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(params, c.mlp_w, MLP_NW * sizeof(float), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(adam_m, c.mlp_m, MLP_NW * sizeof(float), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(adam_v, c.mlp_v, MLP_NW * sizeof(float), cudaMemcpyDeviceToHost, c.s));
+  if (loss) CK(cudaMemcpyAsync(loss, c.mlp_loss, iters * sizeof(float), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  *adam_step = t;
+  // the level operators' W stay those of the active weights
+  return apply_smoother_weights(c, false);
+}
+
 // ---------------------------------------------------------------------------------------
 // setup / upload
 
@@ -657,6 +751,18 @@ static int build_all(Ctx& c, const double* D) {
       if ((st = c.alloc(&lv.resf, lv.n))) return st;
       if ((st = c.alloc(&lv.outf, lv.n))) return st;
     }
+  }
+  // learned-smoother inputs: features and l1 of every smoothed level
+  {
+    std::vector<std::vector<float>> feat;
+    smoother_features(c.H, c.m > 0 ? &J : nullptr, D, c.n, feat);
+    c.feat_d.assign(nlev, nullptr);
+    c.l1_d.assign(nlev, nullptr);
+    for (int l = 0; l + 1 < nlev; ++l) {
+      if ((st = c.upload(&c.feat_d[l], feat[l].data(), (int64_t)feat[l].size()))) return st;
+      if ((st = c.upload(&c.l1_d[l], c.H.l1[l].data(), c.L[l].n))) return st;
+    }
+    if ((st = c.alloc(&c.mlp_w, MLP_NW))) return st;
   }
   c.nL = c.H.n_coarse;
   if (!c.mixed) {
@@ -893,7 +999,9 @@ int amgf_update_D(amgf_handle h, const double* D) {
   if (!h) return fail(AMGF_ERR_INVALID_ARG, "null handle");
   if (h->c.m > 0 && !D) return fail(AMGF_ERR_INVALID_ARG, "null D");
   if (!h->c.host_only) CK(cudaSetDevice(h->c.device));
-  return build_all(h->c, D);
+  const int st = build_all(h->c, D);
+  if (st || h->c.host_only || h->c.mlp_w_host.empty()) return st;
+  return apply_smoother_weights(h->c, false);
 }
 
 int amgf_destroy(amgf_handle h) {
@@ -1016,8 +1124,19 @@ int amgf_pcg_solve(amgf_handle h, const double* b_dev, double* x_dev, amgf_stats
   if (st) return st;
   CK(cudaMemcpyAsync(c.b, b_dev, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
   CK(cudaMemcpyAsync(c.x, x_dev, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
-  const int rs = solve_device(c, stats);
+  int rs = solve_device(c, stats);
   if (rs == AMGF_ERR_CUDA || rs == AMGF_ERR_OOM) return rs;
+  if (stats) stats->mlp_fallback = 0;
+  if (rs != AMGF_OK && !c.mlp_w_host.empty()) {
+    // learned weights failed to reach the stop test: solve again from x0 with theta = 1
+    if ((st = apply_smoother_weights(c, true))) return st;
+    CK(cudaMemcpyAsync(c.x, x_dev, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    rs = solve_device(c, stats);
+    if (stats) stats->mlp_fallback = 1;
+    const int st2 = apply_smoother_weights(c, false);
+    if (rs == AMGF_ERR_CUDA || rs == AMGF_ERR_OOM) return rs;
+    if (st2) return st2;
+  }
   CK(cudaMemcpyAsync(x_dev, c.x, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
   st = join_end(c, stream);
   return st ? st : rs;
@@ -1035,6 +1154,30 @@ int amgf_pcg_solve_host(amgf_handle h, const double* b_host, double* x_host, amg
   CK(cudaMemcpyAsync(x_host, c.x, c.n * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
   return rs;
+}
+
+int amgf_set_mlp(amgf_handle h, const float* weights, int64_t nw) {
+  if (!h) return fail(AMGF_ERR_INVALID_ARG, "null handle");
+  if (h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  Ctx& c = h->c;
+  if (weights && nw != MLP_NW) return fail(AMGF_ERR_INVALID_ARG, "the smoother MLP has 1313 weights");
+  if (weights)
+    for (int64_t k = 0; k < nw; ++k)
+      if (!std::isfinite(weights[k])) return fail(AMGF_ERR_NONFINITE, "non-finite MLP weight");
+  CK(cudaSetDevice(c.device));
+  if (weights) c.mlp_w_host.assign(weights, weights + nw);
+  else c.mlp_w_host.clear();
+  return apply_smoother_weights(c, false);
+}
+
+int amgf_mlp_train(amgf_handle h, float* params, float* adam_m, float* adam_v, int64_t* adam_step, int iters,
+                   float lr, uint64_t seed, float* loss) {
+  if (!h || !params || !adam_m || !adam_v || !adam_step || iters < 0 || !(lr > 0.f))
+    return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  if (h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (h->c.mixed) return fail(AMGF_ERR_INVALID_ARG, "training runs on an FP64 handle (precision 0)");
+  CK(cudaSetDevice(h->c.device));
+  return mlp_train_impl(h->c, params, adam_m, adam_v, adam_step, iters, lr, seed, loss);
 }
 
 int amgf_get_info(amgf_handle h, amgf_info* info) {

@@ -416,11 +416,16 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-// Copy this CTA's rows [r0, r0+nr) of one nb x nb block (row-major, nb even) to shared memory.
-__device__ __forceinline__ void stage_rows(double* dst, const double* blk, int64_t r0, int64_t nr, int64_t nb) {
-  const double* src = blk + r0 * nb;
-  const int64_t chunks = nr * nb / 2;  // 16-byte chunks
-  for (int64_t q = threadIdx.x; q < chunks; q += blockDim.x) cp_async16(dst + 2 * q, src + 2 * q);
+// Copy the rows this warp will use (rr = r0 + warp, r0 + warp + nw, ...) of one nb x nb block
+// (row-major, nb even) to this CTA's staging buffer, whose row q holds block row r0 + q.
+__device__ __forceinline__ void stage_warp_rows(double* dst, const double* blk, int64_t r0, int64_t r1, int64_t nb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t chunks = nb / 2;  // 16-byte chunks per row
+  for (int64_t rr = r0 + warp; rr < r1; rr += nw) {
+    const double* src = blk + rr * nb;
+    double* d = dst + (rr - r0) * nb;
+    for (int64_t q = lane; q < chunks; q += 32) cp_async16(d + 2 * q, src + 2 * q);
+  }
 }
 
 // One dependent step of a block sweep: rows [r0, r1) of  out = vin - M xprev, where M's rows
@@ -477,7 +482,6 @@ filter_sweep_kernel(bool fwd, const double* __restrict__ M, const int64_t* __res
   const int64_t rpc = (nb + cs - 1) / cs;
   const int64_t r0 = rank * rpc < nb ? rank * rpc : nb;
   const int64_t r1 = r0 + rpc < nb ? r0 + rpc : nb;
-  const int64_t nr = r1 - r0;
   // matrix used by step t (t >= 1): forward G_t, backward G_{i+1}^T with i = nblk-1-t
   auto mat_of = [&](int64_t t) -> const double* {
     const int64_t blk = fwd ? t : (nblk - t);
@@ -487,10 +491,12 @@ filter_sweep_kernel(bool fwd, const double* __restrict__ M, const int64_t* __res
   for (int64_t t = 0; t < nblk; ++t) {
     const int cur = (int)(t & 1);
     if (STAGED) {
-      if (t + 1 < nblk) stage_rows(gbuf + ((t + 1) & 1) * rpc * nb, mat_of(t + 1), r0, nr, nb);
+      // each warp stages the rows it will use one step ahead; a warp only reads rows it copied,
+      // so landing its own copies (wait_group) and a warp barrier are enough
+      if (t + 1 < nblk) stage_warp_rows(gbuf + ((t + 1) & 1) * rpc * nb, mat_of(t + 1), r0, r1, nb);
       cp_async_commit();
       cp_async_wait1();  // the copy for step t (committed one iteration earlier) has landed
-      __syncthreads();
+      __syncwarp();
     }
     const int64_t i = fwd ? t : nblk - 1 - t;
     sweep_rows<STAGED>(cluster, cs, xbuf, cur, xbuf + (cur ^ 1) * nb, t > 0, gbuf + cur * rpc * nb,
@@ -532,6 +538,196 @@ __global__ void permute_kernel(int64_t n, const int64_t* __restrict__ scatter_to
     if (scatter_to) out[scatter_to[p]] = in[p];
     else out[p] = in[gather_from[p]];
   }
+}
+
+// ---------------- learned smoother (per-row l1-Jacobi damping) ----------------
+// theta_i = 0.3 + 0.9 sigmoid(MLP(f_i)), MLP 6 -> 32 -> 32 -> 1 with ReLU, weights (1313, FP32):
+//   W1[32][6] | b1[32] | W2[32][32] | b2[32] | w3[32] | b3.   W_i = theta_i / l1_i.
+// theta in [0.3, 1.2] < 2 keeps the l1 smoother convergent and the V-cycle SPD.
+constexpr int MLP_NW = 1313;
+constexpr int MLP_H = 32;
+
+struct MlpAct {
+  float h1[MLP_H], h2[MLP_H];
+  float o;
+};
+
+__device__ __forceinline__ void mlp_forward(const float* w, const float* f, MlpAct& a) {
+  const float* W1 = w;
+  const float* b1 = w + 192;
+  const float* W2 = w + 224;
+  const float* b2 = w + 1248;
+  const float* w3 = w + 1280;
+#pragma unroll 4
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = b1[j];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s += W1[6 * j + k] * f[k];
+    a.h1[j] = s > 0.f ? s : 0.f;
+  }
+#pragma unroll 2
+  for (int j = 0; j < MLP_H; ++j) {
+    float s = b2[j];
+#pragma unroll
+    for (int k = 0; k < MLP_H; ++k) s += W2[MLP_H * j + k] * a.h1[k];
+    a.h2[j] = s > 0.f ? s : 0.f;
+  }
+  float o = w[1312];
+#pragma unroll
+  for (int k = 0; k < MLP_H; ++k) o += w3[k] * a.h2[k];
+  a.o = o;
+}
+
+__device__ __forceinline__ float mlp_sigmoid(float o) { return 1.f / (1.f + __expf(-o)); }
+
+// W = theta / l1 for every row (plain = 1: theta = 1, the plain l1-Jacobi weights)
+__global__ void __launch_bounds__(TPB) mlp_infer_kernel(int64_t n, const float* __restrict__ feat,
+                                                        const float* __restrict__ wglob, int plain,
+                                                        const double* __restrict__ l1, double* winv, float* winvf) {
+  __shared__ float w[MLP_NW];
+  for (int p = threadIdx.x; p < MLP_NW; p += blockDim.x) w[p] = plain ? 0.f : wglob[p];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double theta = 1.0;
+    if (!plain) {
+      float f[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) f[k] = feat[6 * i + k];
+      MlpAct a;
+      mlp_forward(w, f, a);
+      theta = 0.3 + 0.9 * (double)mlp_sigmoid(a.o);
+    }
+    const double wi = theta / l1[i];
+    if (winv) winv[i] = wi;
+    if (winvf) winvf[i] = (float)wi;
+  }
+}
+
+// uniform(-1, 1) training vectors from SplitMix64 (Steele, Lea, Flood) of seed + (i+1) * golden gamma
+__global__ void rand_uniform_kernel(int64_t n, uint64_t seed, double* r) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    r[i] = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+  }
+}
+
+// deterministic dot product: *result = sum a_i b_i
+__global__ void __launch_bounds__(TPB) dot_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                                  double* partial, double* result, unsigned* counter) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  grid_dot_finish(s, partial, result, counter);
+}
+
+// Backward pass of the smoothing loss L = ||e||^2 / ||r||^2, e = (I - A W_theta) r, through the
+// MLP.  dL/dtheta_i = -2 (r_i / l1_i) (A e)_i / ||r||^2 (A symmetric).  One row per thread; the
+// block's 256 rows give one partial gradient (sums over rows in a fixed order), written to
+// partial[blockIdx.x][MLP_NW].  Dynamic shared memory: MLP_SMEM bytes.
+constexpr int MLP_LD = MLP_H + 1;
+constexpr size_t MLP_SMEM = sizeof(float) * (MLP_NW + 4 * TPB * MLP_LD + 6 * TPB + TPB);
+
+__global__ void __launch_bounds__(TPB) mlp_backward_kernel(int64_t n, const float* __restrict__ feat,
+                                                           const float* __restrict__ wglob,
+                                                           const double* __restrict__ r, const double* __restrict__ l1,
+                                                           const double* __restrict__ Ae, const double* rr, float scale,
+                                                           float* partial) {
+  extern __shared__ float msm[];
+  float* w = msm;
+  float* H1 = w + MLP_NW;
+  float* H2 = H1 + TPB * MLP_LD;
+  float* D1 = H2 + TPB * MLP_LD;
+  float* D2 = D1 + TPB * MLP_LD;
+  float* F = D2 + TPB * MLP_LD;
+  float* DO = F + 6 * TPB;
+  for (int p = threadIdx.x; p < MLP_NW; p += blockDim.x) w[p] = wglob[p];
+  __syncthreads();
+  const int t = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * TPB + t;
+  float f[6] = {0, 0, 0, 0, 0, 0};
+  MlpAct a;
+  for (int j = 0; j < MLP_H; ++j) { a.h1[j] = 0.f; a.h2[j] = 0.f; }
+  float dout = 0.f;
+  if (i < n) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) f[k] = feat[6 * i + k];
+    mlp_forward(w, f, a);
+    const float sg = mlp_sigmoid(a.o);
+    const double dth = -2.0 * (r[i] / l1[i]) * Ae[i] / *rr;
+    dout = scale * (float)dth * 0.9f * sg * (1.f - sg);
+  }
+  const float* W2 = w + 224;
+  const float* w3 = w + 1280;
+  float d2[MLP_H];
+  for (int j = 0; j < MLP_H; ++j) d2[j] = (a.h2[j] > 0.f) ? dout * w3[j] : 0.f;
+  for (int k = 0; k < MLP_H; ++k) {
+    float s = 0.f;
+    for (int j = 0; j < MLP_H; ++j) s += W2[MLP_H * j + k] * d2[j];
+    D1[t * MLP_LD + k] = (a.h1[k] > 0.f) ? s : 0.f;
+    H1[t * MLP_LD + k] = a.h1[k];
+    H2[t * MLP_LD + k] = a.h2[k];
+    D2[t * MLP_LD + k] = d2[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) F[6 * t + k] = f[k];
+  DO[t] = dout;
+  __syncthreads();
+  for (int p = t; p < MLP_NW; p += TPB) {
+    float s = 0.f;
+    if (p < 192) {                 // W1[j][k] += d1_j f_k
+      const int j = p / 6, k = p % 6;
+      for (int q = 0; q < TPB; ++q) s += D1[q * MLP_LD + j] * F[6 * q + k];
+    } else if (p < 224) {          // b1
+      const int j = p - 192;
+      for (int q = 0; q < TPB; ++q) s += D1[q * MLP_LD + j];
+    } else if (p < 1248) {         // W2[j][k] += d2_j h1_k
+      const int j = (p - 224) / MLP_H, k = (p - 224) % MLP_H;
+      for (int q = 0; q < TPB; ++q) s += D2[q * MLP_LD + j] * H1[q * MLP_LD + k];
+    } else if (p < 1280) {         // b2
+      const int j = p - 1248;
+      for (int q = 0; q < TPB; ++q) s += D2[q * MLP_LD + j];
+    } else if (p < 1312) {         // w3[k] += dout h2_k
+      const int k = p - 1280;
+      for (int q = 0; q < TPB; ++q) s += DO[q] * H2[q * MLP_LD + k];
+    } else {                       // b3
+      for (int q = 0; q < TPB; ++q) s += DO[q];
+    }
+    partial[(int64_t)blockIdx.x * MLP_NW + p] = s;
+  }
+}
+
+// grad[p] (+)= sum over parts of partial[part][p], parts in index order
+__global__ void mlp_grad_reduce_kernel(int64_t nparts, const float* __restrict__ partial, float* grad, int accumulate) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= MLP_NW) return;
+  float s = 0.f;
+  for (int64_t b = 0; b < nparts; ++b) s += partial[b * MLP_NW + p];
+  grad[p] = accumulate ? grad[p] + s : s;
+}
+
+// Adam (Kingma & Ba) on the MLP parameters
+__global__ void mlp_adam_kernel(float* w, float* m, float* v, const float* __restrict__ g, float lr, float beta1,
+                                float beta2, float eps, float t) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= MLP_NW) return;
+  const float gi = g[p];
+  const float mi = beta1 * m[p] + (1.f - beta1) * gi;
+  const float vi = beta2 * v[p] + (1.f - beta2) * gi * gi;
+  m[p] = mi;
+  v[p] = vi;
+  const float mh = mi / (1.f - powf(beta1, t));
+  const float vh = vi / (1.f - powf(beta2, t));
+  w[p] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// loss[it] = scale * sum_l ee[l] / rr[l]
+__global__ void mlp_loss_kernel(int nl, const double* ee, const double* rr, float scale, float* loss) {
+  double s = 0.0;
+  for (int l = 0; l < nl; ++l) s += ee[l] / rr[l];
+  *loss = (float)(scale * s);
 }
 
 // ---------------- PCG ----------------

@@ -505,6 +505,7 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
     HCSR R = transpose(P);
     HCSR AP = spgemm(A, P);
     HCSR Ac = spgemm(R, AP);
+    H.cf.push_back(cf);
     std::vector<int32_t> fc;
     fc.reserve(nc);
     for (int64_t i = 0; i < n; ++i)
@@ -524,6 +525,42 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
   if (!spd_inverse(dense, nL, H.coarse_inv)) { err = "coarsest matrix is not SPD"; return AMGF_ERR_NOT_SPD; }
   H.n_coarse = nL;
   return AMGF_OK;
+}
+
+void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, int64_t n,
+                       std::vector<std::vector<float>>& feat) {
+  const int nlev = H.nlev();
+  feat.assign(nlev > 1 ? nlev - 1 : 0, std::vector<float>());
+  std::vector<double> d(n, 0.0);
+  std::vector<int8_t> flag(n, 0);
+  if (J && J->nrows > 0)
+    for (int64_t r = 0; r < J->nrows; ++r)
+      for (int64_t k = J->row_ptr[r]; k < J->row_ptr[r + 1]; ++k) {
+        d[J->col_idx[k]] += J->val[k] * (D[r] * J->val[k]);
+        if (J->val[k] != 0.0) flag[J->col_idx[k]] = 1;
+      }
+  for (int l = 0; l + 1 < nlev; ++l) {
+    const HCSR& A = H.A[l];
+    const int64_t nl = A.nrows;
+    std::vector<float>& f = feat[l];
+    f.resize(6 * nl);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nl; ++i) {
+      double aii = 0.0;
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
+        if (A.ci[k] == i) aii = A.v[k];
+      const double l1 = H.l1[l][i];
+      f[6 * i + 0] = (float)(std::log10(aii) / 10.0);
+      f[6 * i + 1] = (float)(std::log10(l1) / 10.0);
+      f[6 * i + 2] = (float)(aii / l1);
+      f[6 * i + 3] = flag[i] ? 1.0f : 0.0f;
+      f[6 * i + 4] = (float)(std::log10(1.0 + d[i]) / 10.0);
+      f[6 * i + 5] = (float)((double)l / (double)(nlev - 1));
+    }
+    int64_t c = 0;
+    for (int64_t i = 0; i < nl; ++i)
+      if (H.cf[l][i]) { d[c] = d[i]; flag[c] = flag[i]; ++c; }
+  }
 }
 
 int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter& F, std::string& err) {

@@ -24,6 +24,7 @@ struct Hierarchy {
   std::vector<HCSR> P, R;                 // P[l]: n_l x n_{l+1}, R[l] = P[l]^T
   std::vector<std::vector<double>> l1;    // l1_i = sum_j |a_ij|
   std::vector<std::vector<int32_t>> func; // unknown (displacement component) of each row
+  std::vector<std::vector<int8_t>> cf;    // C (1) / F (0) split of every coarsened level
   std::vector<double> coarse_inv;         // dense inverse of the coarsest A (row-major)
   int64_t n_coarse = 0;
   int nlev() const { return (int)A.size(); }
@@ -66,6 +67,13 @@ int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, s
 // B := AMG(A): strength, Ruge-Stueben first pass, direct interpolation, Galerkin, l1 sums,
 // dense inverse of the coarsest level.
 int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::string& err);
+
+// Features of the learned smoother for every smoothed level (6 per row, row-major):
+//   log10(a_ii)/10, log10(l1_i)/10, a_ii/l1_i, contact flag, log10(1 + d_i)/10, l/(nlev-1),
+// with d = diag(J^T D J) and the flag (nonzero column of J) on the fine level, carried to a
+// coarse row from the fine C point it comes from.
+void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, int64_t n,
+                       std::vector<std::vector<float>>& feat);
 
 // I_c, A_w = A[I_c, I_c], reverse Cuthill-McKee order, block-tridiagonal LDL^T factor.
 int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter& F, std::string& err);

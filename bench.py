@@ -137,6 +137,16 @@ def cpu_oracle_sample(p, rhs, iters_full: float, sample_iters: int, reps: int = 
     return sec_iter * iters_full, sec_iter, t_setup
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the slowest replica sets the job's time)."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -218,10 +228,7 @@ def run_gpu(args, rank, world, local):
     barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([ms], dist, "cuda")[0]
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     bh = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
@@ -233,10 +240,7 @@ def run_gpu(args, rank, world, local):
         xh[:] = 0.0
         s.pcg_solve_host(bh[k % 3], xh)
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks([e2e_s], dist, "cuda")[0]
 
     # the same workload with the other V-cycle precisions (same timing method, fewer steps),
     # each with its A-norm distance to this run's solution of seed 0
@@ -329,7 +333,8 @@ def run_gpu(args, rank, world, local):
                        "op_complexity": round(float(info.op_complexity), 4), "rtol": 1e-8,
                        "stop": "sqrt(r^T z / r0^T z0)", "pcg_iters": iters,
                        "l2": "working set larger than L2 (no flush)", "setup_s": round(t_setup, 3),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "aggregate_solves_per_s": world / (ms * 1e-3)},
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": int(launches),
             "roofline": roofline,

@@ -43,7 +43,11 @@ WORKLOADS = {
            "FP64 AMGF-PCG",
     "c160": "two-block Q1 elasticity, 160x160x80 elements per block, n=12442080, m=25921, D log-uniform "
             "[1e-2,1e12], FP64 AMGF-PCG",
+    "c202": "two-block Q1 elasticity, 202x202x101 elements per block, n=24972654, m=41209, D log-uniform "
+            "[1e-2,1e12], FP64 AMGF-PCG",
 }
+# learned smoother weights trained by `python -m paper_2505_18576_gb300.learned --config c64 --out ...`
+WEIGHTS = os.path.join(ROOT, "paper_2505_18576_gb300", "weights", "smoother_c64.npz")
 
 
 def dist_env():
@@ -198,6 +202,11 @@ def run_gpu(args, rank, world, local):
     t0 = time.perf_counter()
     s = amgf.Solver(p.K, p.J, p.D, use_graph=0 if args.no_graph else 1, precision=args.precision)
     t_setup = time.perf_counter() - t0
+    weights = None
+    if args.weights:
+        from paper_2505_18576_gb300.learned import load_weights
+        weights = load_weights(WEIGHTS if args.weights == "default" else args.weights)
+        s.set_mlp(weights)
     info = s.info
     n = p.n
     bdev = [torch.from_numpy(b).cuda() for b in rhs]
@@ -215,12 +224,13 @@ def run_gpu(args, rank, world, local):
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters, launches, solve_s = [], 0, []
+    iters, launches, solve_s, fallbacks = [], 0, [], 0
     ev0.record(stream)
     for k in range(args.steps):
         x.zero_()
         st = s.pcg_solve(bdev[k % 3], x, stream=stream)
         iters.append(st.iters)
+        fallbacks += st.mlp_fallback
         launches += st.kernel_launches
         solve_s.append(st.t_solve_s)
     ev1.record(stream)
@@ -248,23 +258,31 @@ def run_gpu(args, rank, world, local):
     if not args.no_variants:
         x_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
         s.pcg_solve(bdev[0], x_ref)
-        Kt = None
-        for prec in (0, 1, 2):
-            if prec == args.precision:
+        table = [("fp64", 0, False), ("fp32_vcycle", 1, False), ("fp32_vcycle_bf16_K", 2, False)]
+        if os.path.exists(WEIGHTS):
+            table.append(("fp32_vcycle_bf16_K_learned", 2, True))
+        wanted = None if args.variants == "all" else set(args.variants.split(","))
+        for name, prec, learned in table:
+            if (prec, learned) == (args.precision, weights is not None) or (wanted and name not in wanted):
                 continue
             sv = amgf.Solver(p.K, p.J, p.D, precision=prec)
+            if learned:
+                from paper_2505_18576_gb300.learned import load_weights
+                sv.set_mlp(load_weights(WEIGHTS))
             xv = torch.zeros(n, dtype=torch.float64, device="cuda")
             for k in range(2):
                 xv.zero_()
                 sv.pcg_solve(bdev[k % 3], xv)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            its = []
+            its, fb = [], 0
             nst = max(2, min(args.steps, 5))
             e0.record(stream)
             for k in range(nst):
                 xv.zero_()
-                its.append(sv.pcg_solve(bdev[k % 3], xv, stream=stream).iters)
+                stv = sv.pcg_solve(bdev[k % 3], xv, stream=stream)
+                its.append(stv.iters)
+                fb += stv.mlp_fallback
             e1.record(stream)
             torch.cuda.synchronize()
             xv.zero_()
@@ -275,9 +293,11 @@ def run_gpu(args, rank, world, local):
             s.matvec(d, yd)
             s.matvec(x_ref, yr)
             rel_a = float(torch.sqrt(torch.dot(d, yd) / torch.dot(x_ref, yr)))
-            variants[{0: "fp64", 1: "fp32_vcycle", 2: "fp32_vcycle_bf16_K"}[prec]] = {
+            variants[name] = {
                 "s_per_solve": e0.elapsed_time(e1) / nst * 1e-3, "pcg_iters": its,
                 "a_norm_rel_diff_vs_timed_solution": rel_a}
+            if learned:
+                variants[name]["mlp_fallbacks"] = fb
             sv.close()
 
     # dominant kernel: the fine-level l1-Jacobi post-smoother (one pass over the fine operator with
@@ -329,11 +349,13 @@ def run_gpu(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": f"{args.config}: {WORKLOADS.get(args.config, args.config)}",
                        "precision": ["fp64", "fp32 V-cycle", "fp32 V-cycle, bf16 fine K"][args.precision],
+                       "smoother": "l1-Jacobi, learned theta (MLP)" if weights is not None else "l1-Jacobi, theta = 1",
                        "n": n, "m": p.m, "nc": int(info.nc), "levels": int(info.nlevels),
                        "op_complexity": round(float(info.op_complexity), 4), "rtol": 1e-8,
                        "stop": "sqrt(r^T z / r0^T z0)", "pcg_iters": iters,
                        "l2": "working set larger than L2 (no flush)", "setup_s": round(t_setup, 3),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "mlp_fallbacks": fallbacks,
                        "aggregate_solves_per_s": world / (ms * 1e-3)},
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": int(launches),
@@ -383,6 +405,11 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="V-cycle precision of the timed solve: 0 FP64, 1 FP32, 2 FP32 with BF16 fine-level K")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant timings")
+    ap.add_argument("--variants", default="all",
+                    help="comma list of variants to time (fp64, fp32_vcycle, fp32_vcycle_bf16_K, "
+                         "fp32_vcycle_bf16_K_learned) or 'all'")
+    ap.add_argument("--weights", default=None,
+                    help="learned smoother weights (.npz) for the timed solve; 'default' = the packaged c64 weights")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the PCG kernels directly instead of one CUDA graph (for per-kernel profiling)")
     args = ap.parse_args()

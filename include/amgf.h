@@ -73,6 +73,10 @@ typedef struct {
                              the outer residual, the dot products, the J^T D J term and the filter
                              solve stay FP64.  2: as 1 with the fine-level K values in BF16.
                              Needs >= 2 levels and 3 unknowns per node, else FP64 is used. */
+  int filter_algo;        /* exact solver of the block-tridiagonal A_w (Section 5.1 filter step; the
+                             paper uses a sparse direct solver): 0 = odd-even block cyclic reduction,
+                             one launch per reduction level (default); 1 = sequential block LDL^T
+                             forward/backward sweeps on one thread-block cluster */
 } amgf_options;
 
 typedef struct {
@@ -135,7 +139,9 @@ int amgf_vcycle(amgf_handle h, const double* r_dev, double* x_dev, void* stream)
 int amgf_matvec(amgf_handle h, const double* x_dev, double* y_dev, void* stream);
 
 /* w_dev = A_w^{-1} v_dev with A_w = A[I_c, I_c] (Section 5.1); v, w of length nc in
- * ascending-DOF order of I_c. */
+ * ascending-DOF order of I_c.  An exact solve up to rounding: A_w is put in reverse
+ * Cuthill-McKee order, where it is block tridiagonal, and solved by odd-even block cyclic
+ * reduction (filter_algo 0) or block LDL^T sweeps (filter_algo 1). */
 int amgf_filter_solve(amgf_handle h, const double* v_dev, double* w_dev, void* stream);
 
 /* Same result as amgf_filter_solve, for callers that cannot allocate device memory while

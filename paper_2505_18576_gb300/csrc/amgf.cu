@@ -1,10 +1,13 @@
 // AMGF-PCG solve phase on one GPU and the C ABI of include/amgf.h.
 //
 // Device layout (one handle):
-//   level l: A_l (CSR, int64 row pointers, int32 columns, FP64 values), P_l, R_l = P_l^T,
-//            W_l = 1 / l1_l, and four n_l-vectors (rhs, x, residual, output);
+//   level l: A_l (CSR, int64 row pointers, int32 columns, FP64 values; the fine level in
+//            3x3 node blocks, 32 block rows per slice), P_l, R_l = P_l^T, W_l = 1 / l1_l,
+//            and four n_l-vectors (rhs, x, residual, output);
 //   coarsest: dense inverse of A_L (FP64);
-//   filter:   block-tridiagonal LDL^T factor of A_w (G_i, G_i^T, D_i^{-1}, nb x nb each),
+//   filter:   the block cyclic reduction of A_w (nb x nb FP64 blocks: eliminated-block
+//             inverses and coupling products, one task list per phase) or, with
+//             filter_algo = 1, its block LDL^T factor (G_i, G_i^T, D_i^{-1});
 //             factor-position -> DOF map, and A[:, I_c] on the rows that touch I_c;
 //   PCG:      x, r, z, p, q, apply scratch (y1, r1), device scalars (PcgState).
 // One AMGF application (Definition "AMGF", Section 5.1):
@@ -52,10 +55,10 @@ struct DCSR {
   int32_t* ci = nullptr;
   double* v = nullptr;
   int K = 4;  // lanes per row
-  // optional 3x3 node-block copy used instead of the CSR arrays (fine level)
+  // optional 3x3 node-block copy (sliced BSR3) used instead of the CSR arrays (fine level)
   bool bsr = false;
-  int64_t nbrows = 0, nblocks = 0;
-  int64_t* brp = nullptr;
+  int64_t nbrows = 0, nslices = 0, nblocks = 0;  // nblocks: stored blocks without padding
+  int64_t* soff = nullptr;
   int32_t* bci = nullptr;
   double* bv = nullptr;
 };
@@ -99,8 +102,8 @@ struct Ctx {
   // mixed precision: fine-level K in 3x3 blocks (FP32 or BF16 planes) + contact term in FP64
   bool mixed = false;
   bool k_bf16 = false;
-  int64_t k_nbrows = 0, k_nblocks = 0;
-  int64_t* k_brp = nullptr;
+  int64_t k_nbrows = 0, k_nslices = 0, k_nblocks = 0;
+  int64_t* k_soff = nullptr;
   int32_t* k_bci = nullptr;
   void* k_v = nullptr;
   int32_t *c_rp = nullptr, *c_ci = nullptr;
@@ -115,6 +118,8 @@ struct Ctx {
   int64_t mlp_part_blocks = 0;
   int mlp_loss_cap = 0;
   double *fG = nullptr, *fGT = nullptr, *fDinv = nullptr, *fy = nullptr, *fz = nullptr, *fw = nullptr, *fv = nullptr;
+  double* fM = nullptr;          // cyclic reduction matrices
+  FilterTask* ftasks = nullptr;  // cyclic reduction task lists of all phases
   int64_t* fgidx = nullptr;
   int64_t* ficidx = nullptr;  // factor position -> index into I_c
   int64_t* ftouch = nullptr;
@@ -227,16 +232,15 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
   c.launches++;
   if (A.bsr && !a.rows) {
     BsrArgs b{};
-    b.brp = A.brp; b.bci = A.bci; b.v = A.bv; b.nbrows = A.nbrows;
+    b.soff = A.soff; b.bci = A.bci; b.v = A.bv; b.nbrows = A.nbrows; b.nslices = A.nslices;
     b.x = a.x; b.b = a.b; b.winv = a.winv; b.w2 = a.w2; b.add = a.add; b.y = a.y; b.y2 = a.y2;
     b.yf = a.yf; b.y2f = a.y2f;
-    constexpr int KB = 4;
-    const int grid = grid_for(c, A.nbrows, KB);
+    const int grid = grid_for(c, A.nslices, 32);  // one warp per slice
     if (result) {
       b.dotv = dotv; b.partial = c.partial; b.result = result; b.counter = c.counter;
-      bsr3_kernel<KB, MODE, true><<<grid, TPB, 0, c.s>>>(b);
+      bsr3_kernel<MODE, true><<<grid, TPB, 0, c.s>>>(b);
     } else {
-      bsr3_kernel<KB, MODE, false><<<grid, TPB, 0, c.s>>>(b);
+      bsr3_kernel<MODE, false><<<grid, TPB, 0, c.s>>>(b);
     }
     return;
   }
@@ -268,11 +272,10 @@ static void launch_csr_f(Ctx& c, const DCSRf& A, CsrArgsT<float> a) {
 template <int MODE>
 static void launch_fine_mixed(Ctx& c, const float* x, const float* b, const float* winv, const double* add,
                               float* y32, double* y64, const double* dotv, double* result) {
-  constexpr int KB = 4;
-  const int grid = grid_for(c, c.k_nbrows, KB);
+  const int grid = grid_for(c, c.k_nslices, 32);  // one warp per slice
   c.launches++;
   auto fill = [&](auto& a) {
-    a.brp = c.k_brp; a.bci = c.k_bci; a.nbrows = c.k_nbrows;
+    a.soff = c.k_soff; a.bci = c.k_bci; a.nbrows = c.k_nbrows; a.nslices = c.k_nslices;
     a.crp = c.c_rp; a.cci = c.c_ci; a.cv = c.c_v;
     a.x = x; a.b = b; a.winv = winv; a.add = add; a.y32 = y32; a.y64 = y64;
     a.dotv = dotv; a.partial = c.partial; a.result = result; a.counter = c.counter;
@@ -281,14 +284,14 @@ static void launch_fine_mixed(Ctx& c, const float* x, const float* b, const floa
     Bsr3MixedArgs<__nv_bfloat16> a{};
     fill(a);
     a.v = (const __nv_bfloat16*)c.k_v;
-    if (result) bsr3_mixed_kernel<__nv_bfloat16, KB, MODE, true><<<grid, TPB, 0, c.s>>>(a);
-    else bsr3_mixed_kernel<__nv_bfloat16, KB, MODE, false><<<grid, TPB, 0, c.s>>>(a);
+    if (result) bsr3_mixed_kernel<__nv_bfloat16, MODE, true><<<grid, TPB, 0, c.s>>>(a);
+    else bsr3_mixed_kernel<__nv_bfloat16, MODE, false><<<grid, TPB, 0, c.s>>>(a);
   } else {
     Bsr3MixedArgs<float> a{};
     fill(a);
     a.v = (const float*)c.k_v;
-    if (result) bsr3_mixed_kernel<float, KB, MODE, true><<<grid, TPB, 0, c.s>>>(a);
-    else bsr3_mixed_kernel<float, KB, MODE, false><<<grid, TPB, 0, c.s>>>(a);
+    if (result) bsr3_mixed_kernel<float, MODE, true><<<grid, TPB, 0, c.s>>>(a);
+    else bsr3_mixed_kernel<float, MODE, false><<<grid, TPB, 0, c.s>>>(a);
   }
 }
 
@@ -462,6 +465,23 @@ static void launch_sweep(Ctx& c, bool fwd, const double* M, const double* r, con
 // directly in factor order by vdirect); y and z are work vectors of the same length
 static void enqueue_filter_solve_into(Ctx& c, const double* r, const double* vdirect, double* y, double* z, double* out) {
   const int64_t nb = c.F.nb, nblk = c.F.nblk;
+  if (c.F.algo == 0) {  // block cyclic reduction: y holds the reduced right-hand sides
+    const int tiles = (int)((nb + FBCR_ROWS - 1) / FBCR_ROWS);
+    const size_t smem = 2 * (size_t)nb * sizeof(double);
+    const int nphase = (int)c.F.phase_off.size() - 1;
+    for (int q = 0; q < nphase; ++q) {
+      const int64_t t0 = c.F.phase_off[q], nt = c.F.phase_off[q + 1] - t0;
+      const unsigned grid = (unsigned)(nt * tiles);
+      if (q == 0)
+        filter_bcr_kernel<true><<<grid, FBCR_TPB, smem, c.s>>>(c.ftasks + t0, tiles, c.fM, nb, r, c.fgidx, vdirect,
+                                                               c.F.nc, y, out);
+      else
+        filter_bcr_kernel<false><<<grid, FBCR_TPB, smem, c.s>>>(c.ftasks + t0, tiles, c.fM, nb, r, c.fgidx, vdirect,
+                                                                c.F.nc, y, out);
+      c.launches++;
+    }
+    return;
+  }
   launch_sweep(c, true, c.fG, r, vdirect, nullptr, y);
   const int64_t rows = nb * nblk;
   int g = (int)((rows * 32 + TPB - 1) / TPB);
@@ -720,10 +740,11 @@ static int build_all(Ctx& c, const double* D) {
         lv.A.nnz = c.H.A[0].nnz();
         lv.A.bsr = true;
         lv.A.nbrows = bsr.nbrows;
-        lv.A.nblocks = (int64_t)bsr.bci.size();
-        if ((st = c.upload(&lv.A.brp, bsr.brp.data(), bsr.nbrows + 1))) return st;
-        if ((st = c.upload(&lv.A.bci, bsr.bci.data(), lv.A.nblocks))) return st;
-        if ((st = c.upload(&lv.A.bv, bsr.v.data(), 9 * lv.A.nblocks))) return st;
+        lv.A.nslices = bsr.nslices;
+        lv.A.nblocks = bsr.nblocks;
+        if ((st = c.upload(&lv.A.soff, bsr.soff.data(), bsr.nslices + 1))) return st;
+        if ((st = c.upload(&lv.A.bci, bsr.bci.data(), (int64_t)bsr.bci.size()))) return st;
+        if ((st = c.upload(&lv.A.bv, bsr.v.data(), (int64_t)bsr.v.size()))) return st;
       } else if ((st = upload_csr(c, c.H.A[l], lv.A))) {
         return st;
       }
@@ -772,9 +793,10 @@ static int build_all(Ctx& c, const double* D) {
     if ((st = c.upload(&c.coarse_inv_f, ci.data(), c.nL * c.nL))) return st;
     // fine-level K in 3x3 blocks, FP32 or BF16 (round to nearest even)
     c.k_nbrows = kb.nbrows;
-    c.k_nblocks = (int64_t)kb.bci.size();
-    if ((st = c.upload(&c.k_brp, kb.brp.data(), kb.nbrows + 1))) return st;
-    if ((st = c.upload(&c.k_bci, kb.bci.data(), c.k_nblocks))) return st;
+    c.k_nslices = kb.nslices;
+    c.k_nblocks = kb.nblocks;
+    if ((st = c.upload(&c.k_soff, kb.soff.data(), kb.nslices + 1))) return st;
+    if ((st = c.upload(&c.k_bci, kb.bci.data(), (int64_t)kb.bci.size()))) return st;
     if (c.k_bf16) {
       std::vector<__nv_bfloat16> v(kb.v.size());
       for (size_t i = 0; i < v.size(); ++i) v[i] = __float2bfloat16_rn((float)kb.v[i]);
@@ -801,9 +823,23 @@ static int build_all(Ctx& c, const double* D) {
   }
   if (c.F.nc > 0) {
     const int64_t tot = c.F.nb * c.F.nblk;
-    if ((st = c.upload(&c.fG, c.F.G.data(), tot * c.F.nb))) return st;
-    if ((st = c.upload(&c.fGT, c.F.GT.data(), tot * c.F.nb))) return st;
-    if ((st = c.upload(&c.fDinv, c.F.Dinv.data(), tot * c.F.nb))) return st;
+    if (c.F.algo == 0) {
+      if (2 * c.F.nb * (int64_t)sizeof(double) > 200 * 1024)
+        return fail(AMGF_ERR_INVALID_ARG, "filter block too large for shared memory");
+      if ((st = c.upload(&c.fM, c.F.M.data(), (int64_t)c.F.M.size()))) return st;
+      if ((st = c.upload(&c.ftasks, c.F.tasks.data(), (int64_t)c.F.tasks.size()))) return st;
+      std::vector<double>().swap(c.F.M);  // the device copy is the only one used
+      if (2 * c.F.nb * (int64_t)sizeof(double) > 48 * 1024)
+        CK(cudaFuncSetAttribute(filter_bcr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * c.F.nb * sizeof(double))));
+      if (2 * c.F.nb * (int64_t)sizeof(double) > 48 * 1024)
+        CK(cudaFuncSetAttribute(filter_bcr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * c.F.nb * sizeof(double))));
+    } else {
+      if ((st = c.upload(&c.fG, c.F.G.data(), tot * c.F.nb))) return st;
+      if ((st = c.upload(&c.fGT, c.F.GT.data(), tot * c.F.nb))) return st;
+      if ((st = c.upload(&c.fDinv, c.F.Dinv.data(), tot * c.F.nb))) return st;
+    }
     if ((st = c.upload(&c.fgidx, c.F.gidx.data(), c.F.nc))) return st;
     std::vector<int64_t> where(c.n, -1), fic(c.F.nc);
     for (int64_t t = 0; t < c.F.nc; ++t) where[c.F.ic[t]] = t;
@@ -817,7 +853,7 @@ static int build_all(Ctx& c, const double* D) {
     if ((st = c.alloc(&c.fv, tot))) return st;
     // filter sweeps: 16-CTA clusters where the device allows them, else 8; stage the next
     // block's rows in shared memory when two stages fit next to the block vectors
-    {
+    if (c.F.algo == 1) {
       const int64_t nb = c.F.nb;
       auto smem_for = [&](int cs, bool staged) {
         const int64_t rpc = (nb + cs - 1) / cs;
@@ -929,6 +965,7 @@ int amgf_options_default(amgf_options* o) {
   o->use_graph = 1;
   o->verbose = 0;
   o->precision = 0;
+  o->filter_algo = 0;
   return AMGF_OK;
 }
 
@@ -953,7 +990,7 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
   if (o) opt = *o; else amgf_options_default(&opt);
   if (opt.nu < 1 || opt.max_levels < 1 || opt.max_coarse < 1 || opt.num_functions < 1 || !(opt.rtol > 0.0) ||
       opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2 || opt.precision < 0 ||
-      opt.precision > 2)
+      opt.precision > 2 || opt.filter_algo < 0 || opt.filter_algo > 1)
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");
@@ -1244,10 +1281,10 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
   const double vec_bytes = which == 0 ? 2.0 * 8.0 * n : 4.0 * 8.0 * n;
   if (which == 2) {  // K blocks (4 or 2 bytes per value + index), contact CSR, 3 FP32 reads + FP64 write
     const double vb = c.k_bf16 ? 2.0 : 4.0;
-    *bytes = (double)c.k_nblocks * (9.0 * vb + 4.0) + (double)(c.k_nbrows + 1) * 8.0 + (n + 1) * 4.0 +
+    *bytes = (double)c.k_nblocks * (9.0 * vb + 4.0) + (double)(c.k_nslices + 1) * 8.0 + (n + 1) * 4.0 +
              3.0 * 4.0 * n + 8.0 * n;
-  } else if (l0.A.bsr)  // 9 values + one block column index per block, block row pointers
-    *bytes = (double)l0.A.nblocks * (9.0 * 8.0 + 4.0) + (double)(l0.A.nbrows + 1) * 8.0 + vec_bytes;
+  } else if (l0.A.bsr)  // 9 values + one block column index per stored block (padding excluded), slice offsets
+    *bytes = (double)l0.A.nblocks * (9.0 * 8.0 + 4.0) + (double)(l0.A.nslices + 1) * 8.0 + vec_bytes;
   else
     *bytes = nnz * 12.0 + (n + 1) * 8.0 + vec_bytes;
   return join_end(c, stream);

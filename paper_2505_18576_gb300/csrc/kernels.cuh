@@ -12,9 +12,12 @@
 //     with W = diag(1 / l1), and optionally a deterministic dot product of the output
 //     with another vector (p^T A p, r^T z) finished by the last block to arrive.
 //   - dense_gemv: coarsest-level solve with the host-computed inverse.
-//   - filter_fwd / filter_bwd: block-tridiagonal LDL^T sweeps of A_w (Section 5.1),
-//     run by one thread-block cluster that keeps the running block vector in
-//     distributed shared memory; filter_diag applies the block pivots in parallel.
+//   - filter_bcr: one phase of the odd-even block cyclic reduction solve of the
+//     block-tridiagonal A_w (Section 5.1 filter step): all block GEMVs of a reduction
+//     level at once over the whole GPU.
+//   - filter_sweep / filter_diag: the alternative sequential block LDL^T sweeps, run by
+//     one thread-block cluster that keeps the running block vector in distributed
+//     shared memory; filter_diag applies the block pivots in parallel.
 //   - PCG scalar/vector kernels with device-resident scalars.
 #pragma once
 
@@ -22,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "setup.h"
 
 namespace amgf {
 
@@ -167,17 +172,16 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T> a) {
   if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
 }
 
-// Fine-level operator in 3x3 node blocks (BSR3).  Block row I (node I) holds nbr blocks;
-// value k (row k/3, column k%3 of the block) of block b of that row sits at
-// v[9*s + k*nbr + b], s = first block of the row, so each of the nine loads of a warp
-// reads consecutive doubles.  One warp per block row, one block per lane; the three row
-// sums are reduced with shuffles and lanes 0..2 write rows 3I..3I+2.  Same epilogues as
-// csr_kernel (SPMV, RESID, PRE, POST, optional deterministic dot).
+// Fine-level operator in 3x3 node blocks (BSR3, slices of 32 block rows; see setup.h):
+// one warp per slice, one lane per block row I, which owns rows 3I..3I+2.  Every load of
+// block values or block columns is one contiguous segment per warp, the slice's blocks are
+// walked in lockstep (no divergence, no shuffles), and each nonzero costs exactly one FP64
+// FMA.  Same epilogues as csr_kernel (SPMV, RESID, RESID_W, POST, optional dot).
 struct BsrArgs {
-  const int64_t* __restrict__ brp;
+  const int64_t* __restrict__ soff;
   const int32_t* __restrict__ bci;
   const double* __restrict__ v;
-  int64_t nbrows;
+  int64_t nbrows, nslices;
   const double* x;
   const double* b;
   const double* winv;
@@ -193,67 +197,56 @@ struct BsrArgs {
   unsigned* counter;
 };
 
-// KB lanes per block row (KB block rows per warp / KB): each lane walks the row's blocks
-// with stride KB; nine plane loads per block read KB consecutive doubles per group.  With
-// FP64 at ~2 FMA/clk/SM on this part the number of FP64 warp instructions per nonzero is
-// what bounds the pass, so groups are kept narrow (few shuffle-add steps).
-template <int KB, int MODE, bool DOT>
+template <int MODE, bool DOT>
 __global__ void __launch_bounds__(TPB) bsr3_kernel(BsrArgs a) {
-  const int lane_w = threadIdx.x & 31;
-  const int sub = lane_w & (KB - 1);
-  const int64_t gid = ((int64_t)blockIdx.x * TPB + threadIdx.x) / KB;
-  const int64_t warp_first = gid - (lane_w / KB);
-  const int64_t stride = (int64_t)gridDim.x * (TPB / KB);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * TPB) >> 5;
   double dacc = 0.0;
-  for (int64_t base = warp_first; base < a.nbrows; base += stride) {
-    const int64_t I = base + lane_w / KB;
-    const bool valid = I < a.nbrows;
+  for (int64_t sl = warp0; sl < a.nslices; sl += nwarp) {
+    const int64_t s0 = a.soff[sl];
+    const int64_t w = (a.soff[sl + 1] - s0) >> 5;
+    const int32_t* ci = a.bci + s0 + lane;
+    const double* vb = a.v + 9 * s0 + lane;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    if (valid) {
-      const int64_t s0 = a.brp[I];
-      const int64_t nbr = a.brp[I + 1] - s0;
-      const double* vb = a.v + 9 * s0;
-      for (int64_t bb = sub; bb < nbr; bb += KB) {
-        const double* p = vb + bb;
-        double m[9];
+#pragma unroll 2
+    for (int64_t j = 0; j < w; ++j) {
+      const int64_t J = __ldg(ci + 32 * j);
+      const double* p = vb + 288 * j;
+      double m[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) m[q] = __ldg(p + q * nbr);
-        const int64_t J = __ldg(a.bci + s0 + bb);
-        const double x0 = __ldg(a.x + 3 * J), x1 = __ldg(a.x + 3 * J + 1), x2 = __ldg(a.x + 3 * J + 2);
-        a0 += m[0] * x0 + m[1] * x1 + m[2] * x2;
-        a1 += m[3] * x0 + m[4] * x1 + m[5] * x2;
-        a2 += m[6] * x0 + m[7] * x1 + m[8] * x2;
-      }
+      for (int q = 0; q < 9; ++q) m[q] = __ldg(p + 32 * q);
+      const double x0 = __ldg(a.x + 3 * J), x1 = __ldg(a.x + 3 * J + 1), x2 = __ldg(a.x + 3 * J + 2);
+      a0 = fma(m[0], x0, a0); a0 = fma(m[1], x1, a0); a0 = fma(m[2], x2, a0);
+      a1 = fma(m[3], x0, a1); a1 = fma(m[4], x1, a1); a1 = fma(m[5], x2, a1);
+      a2 = fma(m[6], x0, a2); a2 = fma(m[7], x1, a2); a2 = fma(m[8], x2, a2);
     }
+    const int64_t I = sl * 32 + lane;
+    if (I < a.nbrows) {
 #pragma unroll
-    for (int off = KB / 2; off > 0; off >>= 1) {  // butterfly: every lane of the group gets all three sums
-      a0 += __shfl_xor_sync(0xffffffffu, a0, off, KB);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, off, KB);
-      a2 += __shfl_xor_sync(0xffffffffu, a2, off, KB);
-    }
-    if (valid && sub < 3) {  // lane c of the group finishes row 3I + c
-      const int c = sub;
-      const double s = c == 0 ? a0 : (c == 1 ? a1 : a2);
-      const int64_t o = 3 * I + c;
-      double out;
-      if (MODE == M_SPMV || MODE == M_SPMV_W) out = s;
-      else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
-      else if (MODE == M_RESID || MODE == M_RESID_W) out = a.b[o] - s;
-      else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
-      a.y[o] = out;
-      if (MODE == M_RESID_W || MODE == M_SPMV_W) {
-        const double w = a.w2[o] * out;
-        if (a.y2) a.y2[o] = w;
-        if (a.y2f) a.y2f[o] = (float)w;
+      for (int c = 0; c < 3; ++c) {  // rows 3I + c
+        const double s = c == 0 ? a0 : (c == 1 ? a1 : a2);
+        const int64_t o = 3 * I + c;
+        double out;
+        if (MODE == M_SPMV || MODE == M_SPMV_W) out = s;
+        else if (MODE == M_SPMV_ADD) out = a.y[o] + s;
+        else if (MODE == M_RESID || MODE == M_RESID_W) out = a.b[o] - s;
+        else { out = a.x[o] + a.winv[o] * (a.b[o] - s); if (a.add) out += a.add[o]; }
+        a.y[o] = out;
+        if (MODE == M_RESID_W || MODE == M_SPMV_W) {
+          const double wv = a.w2[o] * out;
+          if (a.y2) a.y2[o] = wv;
+          if (a.y2f) a.y2f[o] = (float)wv;
+        }
+        if (a.yf) a.yf[o] = (float)out;
+        if (DOT) dacc += a.dotv[o] * out;
       }
-      if (a.yf) a.yf[o] = (float)out;
-      if (DOT) dacc += a.dotv[o] * out;
     }
   }
   if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
 }
 
-// Fine level of the FP32 V-cycle: K in 3x3 node blocks with FP32 or BF16 values (same plane
+// Fine level of the FP32 V-cycle: K in 3x3 node blocks with FP32 or BF16 values (same sliced
 // layout as bsr3_kernel), FP32 vectors and accumulation, plus the contact term
 // J^T D J (entries up to D_max) in FP64 from a CSR over all rows (mostly empty), so that
 //   s_i = (K x)_i [FP32] + (J^T D J x)_i [FP64].
@@ -262,10 +255,10 @@ __global__ void __launch_bounds__(TPB) bsr3_kernel(BsrArgs a) {
 //          V-cycle's output crosses back into the FP64 PCG here)
 template <typename VT>
 struct Bsr3MixedArgs {
-  const int64_t* __restrict__ brp;
+  const int64_t* __restrict__ soff;
   const int32_t* __restrict__ bci;
   const VT* __restrict__ v;
-  int64_t nbrows;
+  int64_t nbrows, nslices;
   const int32_t* __restrict__ crp;  // contact term rows (length n + 1)
   const int32_t* __restrict__ cci;
   const double* __restrict__ cv;
@@ -284,51 +277,45 @@ struct Bsr3MixedArgs {
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename VT, int KB, int MODE, bool DOT>
+template <typename VT, int MODE, bool DOT>
 __global__ void __launch_bounds__(TPB) bsr3_mixed_kernel(Bsr3MixedArgs<VT> a) {
-  const int lane_w = threadIdx.x & 31;
-  const int sub = lane_w & (KB - 1);
-  const int64_t gid = ((int64_t)blockIdx.x * TPB + threadIdx.x) / KB;
-  const int64_t warp_first = gid - (lane_w / KB);
-  const int64_t stride = (int64_t)gridDim.x * (TPB / KB);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * TPB) >> 5;
   double dacc = 0.0;
-  for (int64_t base = warp_first; base < a.nbrows; base += stride) {
-    const int64_t I = base + lane_w / KB;
-    const bool valid = I < a.nbrows;
+  for (int64_t sl = warp0; sl < a.nslices; sl += nwarp) {
+    const int64_t s0 = a.soff[sl];
+    const int64_t w = (a.soff[sl + 1] - s0) >> 5;
+    const int32_t* ci = a.bci + s0 + lane;
+    const VT* vb = a.v + 9 * s0 + lane;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    if (valid) {
-      const int64_t s0 = a.brp[I];
-      const int64_t nbr = a.brp[I + 1] - s0;
-      const VT* vb = a.v + 9 * s0;
-      for (int64_t bb = sub; bb < nbr; bb += KB) {
-        const VT* p = vb + bb;
-        float m[9];
+#pragma unroll 2
+    for (int64_t j = 0; j < w; ++j) {
+      const int64_t J = __ldg(ci + 32 * j);
+      const VT* p = vb + 288 * j;
+      float m[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) m[q] = to_f32(p[q * nbr]);
-        const int64_t J = __ldg(a.bci + s0 + bb);
-        const float x0 = __ldg(a.x + 3 * J), x1 = __ldg(a.x + 3 * J + 1), x2 = __ldg(a.x + 3 * J + 2);
-        a0 += m[0] * x0 + m[1] * x1 + m[2] * x2;
-        a1 += m[3] * x0 + m[4] * x1 + m[5] * x2;
-        a2 += m[6] * x0 + m[7] * x1 + m[8] * x2;
-      }
+      for (int q = 0; q < 9; ++q) m[q] = to_f32(p[32 * q]);
+      const float x0 = __ldg(a.x + 3 * J), x1 = __ldg(a.x + 3 * J + 1), x2 = __ldg(a.x + 3 * J + 2);
+      a0 = fmaf(m[0], x0, a0); a0 = fmaf(m[1], x1, a0); a0 = fmaf(m[2], x2, a0);
+      a1 = fmaf(m[3], x0, a1); a1 = fmaf(m[4], x1, a1); a1 = fmaf(m[5], x2, a1);
+      a2 = fmaf(m[6], x0, a2); a2 = fmaf(m[7], x1, a2); a2 = fmaf(m[8], x2, a2);
     }
+    const int64_t I = sl * 32 + lane;
+    if (I < a.nbrows) {
 #pragma unroll
-    for (int off = KB / 2; off > 0; off >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, off, KB);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, off, KB);
-      a2 += __shfl_xor_sync(0xffffffffu, a2, off, KB);
-    }
-    if (valid && sub < 3) {
-      const int64_t o = 3 * I + sub;
-      double s = (double)(sub == 0 ? a0 : (sub == 1 ? a1 : a2));
-      for (int32_t k = a.crp[o]; k < a.crp[o + 1]; ++k) s += a.cv[k] * (double)a.x[a.cci[k]];
-      if (MODE == M_RESID) {
-        a.y32[o] = (float)((double)a.b[o] - s);
-      } else {
-        double out = (double)a.x[o] + (double)a.winv[o] * ((double)a.b[o] - s);
-        if (a.add) out += a.add[o];
-        a.y64[o] = out;
-        if (DOT) dacc += a.dotv[o] * out;
+      for (int c = 0; c < 3; ++c) {
+        const int64_t o = 3 * I + c;
+        double s = (double)(c == 0 ? a0 : (c == 1 ? a1 : a2));
+        for (int32_t k = a.crp[o]; k < a.crp[o + 1]; ++k) s += a.cv[k] * (double)a.x[a.cci[k]];
+        if (MODE == M_RESID) {
+          a.y32[o] = (float)((double)a.b[o] - s);
+        } else {
+          double out = (double)a.x[o] + (double)a.winv[o] * ((double)a.b[o] - s);
+          if (a.add) out += a.add[o];
+          a.y64[o] = out;
+          if (DOT) dacc += a.dotv[o] * out;
+        }
       }
     }
   }
@@ -503,6 +490,63 @@ filter_sweep_kernel(bool fwd, const double* __restrict__ M, const int64_t* __res
                        t > 0 ? mat_of(t) : M, r0, r1, nb, i * nb, fwd ? nc : 0, r, gidx, vdirect,
                        fwd ? nullptr : zin, out);
     cluster.sync();
+  }
+}
+
+// One phase of the block cyclic reduction solve of A_w (tasks built on the host, see
+// FilterTask).  CTA = (task, tile of FBCR_ROWS output rows); the task's input blocks are
+// staged in shared memory, eight lanes reduce one row of each nb x nb GEMV (row-major,
+// coalesced) with two independent FMA chains.  GATHER: the phase reads the right-hand
+// side v straight from r[gidx[p]] (or vdirect[p]) in factor order, 0 on padding rows.
+constexpr int FBCR_TPB = 256;
+constexpr int FBCR_ROWS = FBCR_TPB / 8;
+
+template <bool GATHER>
+__global__ void __launch_bounds__(FBCR_TPB)
+filter_bcr_kernel(const FilterTask* __restrict__ tasks, int tiles, const double* __restrict__ M, int64_t nb,
+                  const double* __restrict__ r, const int64_t* __restrict__ gidx, const double* __restrict__ vdirect,
+                  int64_t nc, double* v, double* x) {
+  extern __shared__ __align__(16) double fin[];  // [2][nb]: input blocks in0, in1
+  const FilterTask t = tasks[blockIdx.x / tiles];
+  const int64_t tile = blockIdx.x % tiles;
+  auto vin = [&](int64_t p) -> double {
+    if (GATHER) return p < nc ? (vdirect ? vdirect[p] : r[gidx[p]]) : 0.0;
+    return v[p];
+  };
+  auto stage = [&](int32_t blk, double* dst) {
+    if (blk < 0) return;
+    const int64_t base = (int64_t)blk * nb;
+    for (int64_t q = threadIdx.x; q < nb; q += FBCR_TPB) dst[q] = t.kind == 2 ? x[base + q] : vin(base + q);
+  };
+  stage(t.in0, fin);
+  stage(t.in1, fin + nb);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 3, sub = lane & 7;
+  const int64_t row = tile * FBCR_ROWS + (threadIdx.x >> 5) * 4 + g;
+  double sa = 0.0, sb = 0.0;
+  auto term = [&](int64_t mat, int32_t blk, const double* xv) {
+    if (mat < 0 || blk < 0) return;
+    const double* mr = M + mat * nb * nb + row * nb;
+    int64_t c = sub;
+    for (; c + 8 < nb; c += 16) {
+      sa = fma(__ldg(mr + c), xv[c], sa);
+      sb = fma(__ldg(mr + c + 8), xv[c + 8], sb);
+    }
+    if (c < nb) sa = fma(__ldg(mr + c), xv[c], sa);
+  };
+  if (row < nb) {
+    term(t.m0, t.in0, fin);
+    term(t.m1, t.in1, fin + nb);
+  }
+  double s = sa + sb;
+  s += __shfl_xor_sync(0xffffffffu, s, 4, 8);
+  s += __shfl_xor_sync(0xffffffffu, s, 2, 8);
+  s += __shfl_xor_sync(0xffffffffu, s, 1, 8);
+  if (row < nb && sub == 0) {
+    const int64_t p = (int64_t)t.out * nb + row;
+    if (t.kind == 0) x[p] = s;
+    else if (t.kind == 1) v[p] = vin(p) - s;
+    else x[p] = x[p] - s;
   }
 }
 

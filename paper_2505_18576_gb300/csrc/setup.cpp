@@ -296,6 +296,9 @@ bool cholesky(std::vector<double>& a, int64_t n) {
 bool spd_inverse(const std::vector<double>& a, int64_t n, std::vector<double>& inv) {
   std::vector<double> L(a);
   if (!cholesky(L, n)) return false;
+  std::vector<double> Lt(n * n);  // L^T row-major: the backward pass reads rows
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = 0; k < n; ++k) Lt[i * n + k] = L[k * n + i];
   inv.assign(n * n, 0.0);
 #pragma omp parallel for schedule(dynamic, 4) if (n > 64)
   for (int64_t c = 0; c < n; ++c) {
@@ -307,7 +310,7 @@ bool spd_inverse(const std::vector<double>& a, int64_t n, std::vector<double>& i
     }
     for (int64_t i = n - 1; i >= 0; --i) {
       double s = y[i];
-      for (int64_t k = i + 1; k < n; ++k) s -= L[k * n + i] * y[k];
+      for (int64_t k = i + 1; k < n; ++k) s -= Lt[i * n + k] * y[k];
       y[i] = s / L[i * n + i];
     }
     for (int64_t i = 0; i < n; ++i) inv[i * n + c] = y[i];
@@ -336,13 +339,151 @@ void gemm(int64_t n, const double* A, const double* B, double* C, double alpha, 
   }
 }
 
+// C = alpha * op(A) * B + beta * C for n x n row-major blocks, op(A) = A or A^T; tiled over
+// (i, k) so that a 64-row panel of B stays in cache.  Parallel over row tiles unless called
+// from inside a parallel region.
+void gemm_nn(int64_t n, const double* A, bool transA, const double* B, double* C, double alpha, double beta) {
+  constexpr int64_t T = 64;
+  const int64_t ntile = (n + T - 1) / T;
+#pragma omp parallel for schedule(static) if (!omp_in_parallel() && n >= 2 * T)
+  for (int64_t it = 0; it < ntile; ++it) {
+    const int64_t i0 = it * T, i1 = std::min(n, i0 + T);
+    std::vector<double> acc((i1 - i0) * n, 0.0);
+    for (int64_t k0 = 0; k0 < n; k0 += T) {
+      const int64_t k1 = std::min(n, k0 + T);
+      for (int64_t i = i0; i < i1; ++i) {
+        double* ar = acc.data() + (i - i0) * n;
+        for (int64_t k = k0; k < k1; ++k) {
+          const double a = transA ? A[k * n + i] : A[i * n + k];
+          if (a == 0.0) continue;
+          const double* b = B + k * n;
+          for (int64_t j = 0; j < n; ++j) ar[j] += a * b[j];
+        }
+      }
+    }
+    for (int64_t i = i0; i < i1; ++i)
+      for (int64_t j = 0; j < n; ++j)
+        C[i * n + j] = alpha * acc[(i - i0) * n + j] + (beta == 0.0 ? 0.0 : beta * C[i * n + j]);
+  }
+}
+
+std::vector<double> transpose_block(int64_t n, const std::vector<double>& a) {
+  std::vector<double> t(n * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) t[j * n + i] = a[i * n + j];
+  return t;
+}
+
+// Odd-even block cyclic reduction of the symmetric block-tridiagonal matrix with diagonal
+// blocks A_k and sub-diagonal blocks L_k = A_{k,k-1} (k = 0..N-1).  Eliminating the odd
+// blocks x_k = A_k^{-1} (v_k - L_k x_{k-1} - L_{k+1}^T x_{k+1}) from the even rows leaves a
+// block-tridiagonal system on the even blocks:
+//   A'_k = A_k - E_k L_k^T - F_k L_{k+1},   L'_k = -E_k L_{k-1},   v'_k = v_k - E_k v_{k-1} - F_k v_{k+1}
+// with E_k = L_k A_{k-1}^{-1} and F_k = L_{k+1}^T A_{k+1}^{-1}; the back substitution is
+// x_k = A_k^{-1} v_k - F_{k-1}^T x_{k-1} - E_{k+1}^T x_{k+1}.  This is block Gaussian
+// elimination of A_w in odd-even order, so the solve stays exact up to rounding.
+int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<double>& As, Filter& F,
+              std::string& err) {
+  const int64_t bsz = nb * nb;
+  int64_t N = nblk, stride = 1;
+  std::vector<std::vector<double>> A(N), L(N);
+  for (int64_t k = 0; k < N; ++k) {
+    A[k].assign(Ad.begin() + k * bsz, Ad.begin() + (k + 1) * bsz);
+    if (k > 0) L[k].assign(As.begin() + k * bsz, As.begin() + (k + 1) * bsz);
+  }
+  std::vector<double>().swap(Ad);
+  std::vector<double>().swap(As);
+  F.M.clear();
+  auto push = [&](const std::vector<double>& m) {
+    const int64_t idx = (int64_t)(F.M.size() / bsz);
+    F.M.insert(F.M.end(), m.begin(), m.end());
+    return idx;
+  };
+  std::vector<std::vector<FilterTask>> fwd, bwd;
+  bool spd = true;
+  while (N > 1) {
+    std::vector<std::vector<double>> Ainv(N), E(N), Fk(N);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 1; k < N; k += 2) {
+      std::vector<double> inv;
+      if (!spd_inverse(A[k], nb, inv)) {
+#pragma omp critical
+        spd = false;
+      }
+      Ainv[k].swap(inv);
+    }
+    if (!spd) { err = "filter matrix A_w is not SPD"; return AMGF_ERR_NOT_SPD; }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < N; k += 2) {
+      if (k >= 1) { E[k].resize(bsz); gemm_nn(nb, L[k].data(), false, Ainv[k - 1].data(), E[k].data(), 1.0, 0.0); }
+      if (k + 1 < N) { Fk[k].resize(bsz); gemm_nn(nb, L[k + 1].data(), true, Ainv[k + 1].data(), Fk[k].data(), 1.0, 0.0); }
+    }
+    const int64_t N2 = (N + 1) / 2;
+    std::vector<std::vector<double>> A2(N2), L2(N2);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < N; k += 2) {
+      std::vector<double> a = A[k];
+      if (k >= 1) {
+        const std::vector<double> LT = transpose_block(nb, L[k]);
+        gemm_nn(nb, E[k].data(), false, LT.data(), a.data(), -1.0, 1.0);
+      }
+      if (k + 1 < N) gemm_nn(nb, Fk[k].data(), false, L[k + 1].data(), a.data(), -1.0, 1.0);
+      for (int64_t r = 0; r < nb; ++r)
+        for (int64_t c = r + 1; c < nb; ++c) {
+          const double sym = 0.5 * (a[r * nb + c] + a[c * nb + r]);
+          a[r * nb + c] = a[c * nb + r] = sym;
+        }
+      A2[k / 2].swap(a);
+      if (k >= 2) {
+        L2[k / 2].resize(bsz);
+        gemm_nn(nb, E[k].data(), false, L[k - 1].data(), L2[k / 2].data(), -1.0, 0.0);
+      }
+    }
+    std::vector<FilterTask> tf, tb;
+    for (int64_t k = 0; k < N; ++k) {
+      const int32_t o = (int32_t)(k * stride);
+      if (k & 1) {
+        tf.push_back({push(Ainv[k]), -1, o, o, -1, 0});
+        const int64_t mb = push(transpose_block(nb, Fk[k - 1]));
+        const int64_t mc = k + 1 < N ? push(transpose_block(nb, E[k + 1])) : -1;
+        tb.push_back({mb, mc, o, (int32_t)((k - 1) * stride), k + 1 < N ? (int32_t)((k + 1) * stride) : -1, 2});
+      } else {
+        const int64_t me = k >= 1 ? push(E[k]) : -1;
+        const int64_t mf = k + 1 < N ? push(Fk[k]) : -1;
+        tf.push_back({me, mf, o, k >= 1 ? (int32_t)((k - 1) * stride) : -1,
+                      k + 1 < N ? (int32_t)((k + 1) * stride) : -1, 1});
+      }
+    }
+    fwd.push_back(std::move(tf));
+    bwd.push_back(std::move(tb));
+    A.swap(A2);
+    L.swap(L2);
+    N = N2;
+    stride *= 2;
+  }
+  std::vector<double> inv0;
+  if (!spd_inverse(A[0], nb, inv0)) { err = "filter matrix A_w is not SPD"; return AMGF_ERR_NOT_SPD; }
+  const int64_t m0 = push(inv0);
+  F.bcr_levels = (int)fwd.size();
+  F.tasks.clear();
+  F.phase_off.assign(1, 0);
+  auto add_phase = [&](const std::vector<FilterTask>& t) {
+    F.tasks.insert(F.tasks.end(), t.begin(), t.end());
+    F.phase_off.push_back((int64_t)F.tasks.size());
+  };
+  for (const auto& t : fwd) add_phase(t);
+  add_phase({FilterTask{m0, -1, 0, 0, -1, 0}});
+  for (int64_t l = (int64_t)bwd.size() - 1; l >= 0; --l) add_phase(bwd[l]);
+  return AMGF_OK;
+}
+
 }  // namespace
 
 bool build_bsr3(const HCSR& A, double max_fill, BSR3& out) {
   out = BSR3();
   if (A.nrows % 3 != 0 || A.nrows != A.ncols || A.nrows == 0) return false;
   const int64_t nb = A.nrows / 3;
-  std::vector<int64_t> cnt(nb + 1, 0);
+  std::vector<int64_t> cnt(nb, 0);
   auto block_cols = [&](int64_t I, std::vector<int32_t>& cols) {
     cols.clear();
     for (int r = 0; r < 3; ++r)
@@ -354,29 +495,45 @@ bool build_bsr3(const HCSR& A, double max_fill, BSR3& out) {
   {
     std::vector<int32_t> cols;
 #pragma omp for schedule(static)
-    for (int64_t I = 0; I < nb; ++I) { block_cols(I, cols); cnt[I + 1] = (int64_t)cols.size(); }
+    for (int64_t I = 0; I < nb; ++I) { block_cols(I, cols); cnt[I] = (int64_t)cols.size(); }
   }
-  for (int64_t I = 0; I < nb; ++I) cnt[I + 1] += cnt[I];
-  if ((double)cnt[nb] * 9.0 > max_fill * (double)A.nnz()) return false;
+  int64_t nblocks = 0;
+  for (int64_t I = 0; I < nb; ++I) nblocks += cnt[I];
+  if ((double)nblocks * 9.0 > max_fill * (double)A.nnz()) return false;
+  const int64_t ns = (nb + BSR3::W - 1) / BSR3::W;
   out.nbrows = nb;
-  out.brp = cnt;
-  out.bci.resize(cnt[nb]);
-  out.v.assign(9 * cnt[nb], 0.0);
+  out.nslices = ns;
+  out.nblocks = nblocks;
+  out.soff.assign(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int64_t w = 0;
+    for (int64_t I = sl * BSR3::W; I < std::min(nb, (sl + 1) * BSR3::W); ++I) w = std::max(w, cnt[I]);
+    out.soff[sl + 1] = out.soff[sl] + BSR3::W * w;
+  }
+  const int64_t slots = out.soff[ns];
+  out.bci.assign(slots, 0);
+  out.v.assign(9 * slots, 0.0);
 #pragma omp parallel
   {
     std::vector<int32_t> cols;
 #pragma omp for schedule(static)
-    for (int64_t I = 0; I < nb; ++I) {
-      block_cols(I, cols);
-      const int64_t s0 = out.brp[I], nbr = (int64_t)cols.size();
-      std::copy(cols.begin(), cols.end(), out.bci.begin() + s0);
-      for (int r = 0; r < 3; ++r) {
-        size_t b = 0;
-        for (int64_t k = A.rp[3 * I + r]; k < A.rp[3 * I + r + 1]; ++k) {
-          const int32_t J = A.ci[k] / 3;
-          while (cols[b] < J) ++b;
-          const int c = A.ci[k] % 3;
-          out.v[9 * s0 + (3 * r + c) * nbr + b] = A.v[k];
+    for (int64_t sl = 0; sl < ns; ++sl) {
+      const int64_t s0 = out.soff[sl], w = (out.soff[sl + 1] - s0) / BSR3::W;
+      for (int lane = 0; lane < BSR3::W; ++lane) {
+        const int64_t I = sl * BSR3::W + lane;
+        const int32_t pad = (int32_t)std::min(I, nb - 1);  // padding slots: own block row, zero values
+        for (int64_t j = 0; j < w; ++j) out.bci[s0 + BSR3::W * j + lane] = pad;
+        if (I >= nb) continue;
+        block_cols(I, cols);
+        for (size_t j = 0; j < cols.size(); ++j) out.bci[s0 + BSR3::W * j + lane] = cols[j];
+        for (int r = 0; r < 3; ++r) {
+          size_t b = 0;
+          for (int64_t k = A.rp[3 * I + r]; k < A.rp[3 * I + r + 1]; ++k) {
+            const int32_t J = A.ci[k] / 3;
+            while (cols[b] < J) ++b;
+            const int c = A.ci[k] % 3;
+            out.v[9 * s0 + (9 * (int64_t)b + 3 * r + c) * BSR3::W + lane] = A.v[k];
+          }
         }
       }
     }
@@ -686,6 +843,11 @@ int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter
     }
   }
   for (int64_t p = nc; p < nblk * nb; ++p) Ad[(p / nb) * bsz + (p % nb) * nb + (p % nb)] = 1.0;
+  F.algo = o.filter_algo == 1 ? 1 : 0;
+  if (F.algo == 0) {
+    const int st = build_bcr(nb, nblk, Ad, As, F, err);
+    if (st) return st;
+  } else {
   // block LDL^T: D_0 = A_00; G_i = A_{i,i-1} D_{i-1}^{-1}; D_i = A_ii - G_i A_{i-1,i}
   F.Dinv.assign(nblk * bsz, 0.0);
   F.G.assign(nblk * bsz, 0.0);
@@ -710,6 +872,7 @@ int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter
     std::vector<double> inv;
     if (!spd_inverse(Dcur, nb, inv)) { err = "filter matrix A_w is not SPD"; return AMGF_ERR_NOT_SPD; }
     std::copy(inv.begin(), inv.end(), F.Dinv.begin() + i * bsz);
+  }
   }
   // A[:, I_c] on the rows that touch I_c, columns as factor positions
   std::vector<int64_t> rowcnt(n, 0);

@@ -30,31 +30,56 @@ struct Hierarchy {
   int nlev() const { return (int)A.size(); }
 };
 
+// One output block of a block cyclic reduction phase (all block indices are positions in
+// the original block order; matrices are offsets in units of nb*nb doubles, -1 = absent):
+//   kind 0: x[out] = M[m0] v[in0]                       (eliminated block: u = A^{-1} v)
+//   kind 1: v[out] = v[out] - M[m0] v[in0] - M[m1] v[in1]   (kept block: reduced right side)
+//   kind 2: x[out] = x[out] - M[m0] x[in0] - M[m1] x[in1]   (back substitution)
+struct FilterTask {
+  int64_t m0, m1;
+  int32_t out, in0, in1, kind;
+};
+
 struct Filter {
   int64_t nc = 0;                 // |I_c|
   std::vector<int64_t> ic;        // I_c, ascending DOF indices
   std::vector<int64_t> gidx;      // factor position p -> DOF index (p < nc)
   int64_t nb = 0, nblk = 0;       // block size, number of diagonal blocks (nblk*nb >= nc)
+  int algo = 0;                   // 0: block cyclic reduction, 1: sequential block LDL^T sweeps
+  // algo 1: block LDL^T
   std::vector<double> Dinv;       // nblk blocks nb x nb: inverse of the block pivots D_i
   std::vector<double> G;          // nblk blocks: G_i = A_{i,i-1} D_{i-1}^{-1} (G_0 = 0)
   std::vector<double> GT;         // transposes of G_i
+  // algo 0: odd-even block cyclic reduction; matrices nb x nb row-major in M, one task list
+  // per phase: phases 0..L-1 reduce level 0..L-1, phase L solves the last block, phases
+  // L+1..2L substitute back through levels L-1..0
+  std::vector<double> M;
+  std::vector<FilterTask> tasks;
+  std::vector<int64_t> phase_off; // tasks of phase q: [phase_off[q], phase_off[q+1])
+  int bcr_levels = 0;             // L
   // A[:, I_c] restricted to rows that touch I_c; columns are factor positions p
   std::vector<int64_t> touch_rows;
   HCSR Sc;
 };
 
-// Fine-level operator in 3x3 node blocks, values stored row-block-wise as nine
-// consecutive planes: v[9*s + k*nbr + b] = entry k (row k/3, col k%3) of block b of a
-// block row whose first block is s and which has nbr blocks.
+// Fine-level operator in 3x3 node blocks, in slices of W = 32 consecutive block rows (one
+// GPU lane per block row): slice s has width w_s = the longest block row of the slice and
+// owns slots soff[s] .. soff[s] + 32 w_s; block j of block row I = 32 s + lane sits in slot
+// soff[s] + 32 j + lane, its column in bci[slot] and its value k (row k/3, column k%3) at
+// v[9 soff[s] + (9 j + k) 32 + lane].  A warp's load of one value of block j of its 32 rows
+// is one contiguous segment.  Padding slots (j beyond the row's length, rows past the end)
+// hold zero values and the row's own block column.
 struct BSR3 {
-  int64_t nbrows = 0;
-  std::vector<int64_t> brp;
+  static constexpr int64_t W = 32;
+  int64_t nbrows = 0, nslices = 0;
+  int64_t nblocks = 0;            // stored blocks, padding excluded
+  std::vector<int64_t> soff;      // nslices + 1, multiples of W
   std::vector<int32_t> bci;
   std::vector<double> v;
 };
 
-// Converts A to BSR3 when n % 3 == 0 and the explicit zero fill stays below `max_fill`
-// (stored values / nnz); returns false otherwise.
+// Converts A to BSR3 when n % 3 == 0 and the explicit zero fill inside the blocks stays
+// below `max_fill` (9 x blocks / nnz); returns false otherwise.
 bool build_bsr3(const HCSR& A, double max_fill, BSR3& out);
 
 // Input validation; returns an amgf_status.
@@ -75,7 +100,8 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
 void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, int64_t n,
                        std::vector<std::vector<float>>& feat);
 
-// I_c, A_w = A[I_c, I_c], reverse Cuthill-McKee order, block-tridiagonal LDL^T factor.
+// I_c, A_w = A[I_c, I_c], reverse Cuthill-McKee order, and the exact solver of the
+// block-tridiagonal A_w: block cyclic reduction (o.filter_algo 0) or block LDL^T (1).
 int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter& F, std::string& err);
 
 }  // namespace amgf

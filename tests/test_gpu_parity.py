@@ -5,7 +5,8 @@ tests/test_library_host.py, so every difference comes from the order of operatio
   - A x: per row, |y_gpu - y_orc| <= 2 gamma_k (|A| |x|)_i, gamma_k = k u / (1 - k u), k = nonzeros
     of the row (forward error bound of a dot product, applied to both sides).
   - V-cycle: ||x_gpu - x_orc|| <= 1e-12 ||x_orc||.
-  - Filter solve w = A_w^{-1} v: both sides are exact solves (banded Cholesky vs block LDL^T);
+  - Filter solve w = A_w^{-1} v: both sides are exact solves (banded Cholesky vs block cyclic
+    reduction, or block LDL^T sweeps with filter_algo = 1);
     two such FP64 solves agree only to ~ kappa(A_w) u, and kappa(A_w) grows with the spread of D
     (D couples the two contact faces).  Asserted: normwise backward error <= 64 u on the GPU
     result, and ||w_gpu - w_orc|| <= max(1e-12, 16 u kappa(A_w)) ||w_orc||.
@@ -116,6 +117,26 @@ def test_filter_solve_parity(case):
     back = np.linalg.norm(Aw @ wg - v) / (np.linalg.norm(Aw, 2) * np.linalg.norm(wg))
     assert back <= 64 * EPS
     assert np.linalg.norm(wg - wo) <= max(1e-12, 16 * EPS * kap) * np.linalg.norm(wo)
+
+
+def test_filter_sweep_algorithm_parity(case):
+    # the alternative exact solver (sequential block LDL^T sweeps on one cluster) meets the same bounds
+    import paper_2505_18576_gb300 as m
+    name, p, o, _ = case
+    kap, Aw = kappa_Aw(o)
+    s1 = m.Solver(p.K, p.J, p.D, filter_algo=1)
+    try:
+        rng = np.random.default_rng(2)
+        v = rng.standard_normal(o.nc)
+        w = torch.empty(o.nc, dtype=torch.float64, device="cuda")
+        s1.filter_solve(dev(v), w)
+        wg = host(w)
+        wo = o.filter_solve(v)
+        back = np.linalg.norm(Aw @ wg - v) / (np.linalg.norm(Aw, 2) * np.linalg.norm(wg))
+        assert back <= 64 * EPS
+        assert np.linalg.norm(wg - wo) <= max(1e-12, 16 * EPS * kap) * np.linalg.norm(wo)
+    finally:
+        s1.close()
 
 
 def test_apply_parity(case):

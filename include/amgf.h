@@ -56,7 +56,7 @@ typedef struct {
 } amgf_csr;
 
 typedef struct {
-  double strength_theta;  /* AMG strength threshold (0.8) */
+  double strength_theta;  /* AMG strength threshold (0.55) */
   double rtol;            /* PCG stop: sqrt(r^T z / r0^T z0) < rtol (1e-8); Section 4 uses this norm */
   int max_levels;         /* AMG levels including the coarsest (25) */
   int max_coarse;         /* stop coarsening at n_l <= max_coarse (128); coarsest solved exactly */
@@ -77,6 +77,10 @@ typedef struct {
                              paper uses a sparse direct solver): 0 = odd-even block cyclic reduction,
                              one launch per reduction level (default); 1 = sequential block LDL^T
                              forward/backward sweeps on one thread-block cluster */
+  int interp;             /* AMG interpolation: 0 = classical Ruge-Stueben interpolation (strong F
+                             neighbours distributed over the strong C points, weak ones lumped;
+                             rows whose lumped diagonal nearly vanishes use direct weights), the
+                             default; 1 = direct interpolation with Stueben's sign split */
 } amgf_options;
 
 typedef struct {

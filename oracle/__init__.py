@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("strength_theta", ctypes.c_double), ("max_coarse", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("num_functions", ctypes.c_int),
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int),
-                ("contact_components", ctypes.c_int), ("build_amg", ctypes.c_int)]
+                ("contact_components", ctypes.c_int), ("build_amg", ctypes.c_int),
+                ("interp", ctypes.c_int)]
 
 
 def _load():

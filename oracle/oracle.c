@@ -26,8 +26,15 @@
  *               (each new F point raises the measure of its undecided influencers by 1); the new
  *               C point lowers the measure of its undecided influencers by 1; when the maximal
  *               measure is 0, leftover points become C if they have a strong influencer, else F
- *   interp    : direct interpolation with the sign split; sums over same-function neighbours;
- *               positive entries lumped into the diagonal when no positive strong C neighbour
+ *   interp    : classical interpolation (Ruge-Stueben): strong C neighbours interpolate
+ *               directly, each strong F neighbour k is distributed over the strong C points
+ *               of i in proportion to the entries of row k whose sign is opposite to a_kk's,
+ *               weak neighbours (and strong F points with an empty distribution) are lumped
+ *               into the diagonal; a row whose lumped diagonal falls below 5% of a_ii in
+ *               magnitude takes direct interpolation with the sign split instead (positive
+ *               entries lumped into the diagonal when no positive strong C neighbour).  Only
+ *               same-function couplings enter.  interp = 1 selects direct interpolation
+ *               everywhere.
  *   Galerkin  : R = P^T, A_c = R (A P); every sum taken in ascending index order
  *   smoother  : nu sweeps of x <- x + (r - A x) / l1, l1_i = sum_j |a_ij|, zero start on the way
  *               down and the same sweeps on the way up (B symmetric)
@@ -68,6 +75,7 @@ typedef struct {
   int filter;            /* 0: M = B (AMG-PCG); 1: AMGF */
   int contact_components;/* 0: I_c = nonzero columns of J; 1: all 3 DOFs of those nodes; 2: all DOFs */
   int build_amg;         /* 1: full setup; 0: assemble A only (for A x on large problems) */
+  int interp;            /* 0: classical interpolation (default); 1: direct interpolation */
 } orc_opts;
 
 typedef struct {
@@ -335,9 +343,43 @@ static void rs_coarsen(const ocsr* Sg, int8_t* cf) {
   csr_free(&St);
 }
 
-/* direct interpolation (sign split) */
-static void direct_interp(const ocsr* A, const ocsr* Sg, const int32_t* func, const int8_t* cf,
-                          ocsr* P, int64_t* ncoarse) {
+/* Direct interpolation weights of F point i (Stueben's sign split, same-function sums):
+ * appended at P->ci/P->v[*nnz...]; strong[] marks the strong neighbours of i. */
+static void direct_row(const ocsr* A, int64_t i, const int32_t* func, const int8_t* strong,
+                       const int64_t* cidx, ocsr* P, int64_t* nnz) {
+  double diag = 0.0, sn = 0.0, sp = 0.0, cn = 0.0, cp = 0.0;
+  for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+    int64_t j = A->ci[k];
+    double a = A->v[k];
+    if (j == i) { diag = a; continue; }
+    if (func[j] != func[i]) continue;
+    if (a < 0.0) sn += a; else sp += a;
+    if (strong[j] && cidx[j] >= 0) { if (a < 0.0) cn += a; else cp += a; }
+  }
+  if (cp == 0.0) diag += sp;
+  double alpha = (cn != 0.0) ? sn / cn : 0.0;
+  double beta = (cp != 0.0) ? sp / cp : 0.0;
+  for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+    int64_t j = A->ci[k];
+    if (j == i || !strong[j] || cidx[j] < 0) continue;
+    double a = A->v[k];
+    double w = (a < 0.0) ? -(alpha * a) / diag : -(beta * a) / diag;
+    P->ci[*nnz] = (int32_t)cidx[j]; P->v[*nnz] = w; (*nnz)++;
+  }
+}
+
+/* Interpolation P (n x n_c) from the C/F split.
+ * interp = 0, classical interpolation (Ruge & Stueben), same-function couplings only:
+ *   w_ij = -( a_ij + sum_{k in F_i^s} a_ik abar_kj / sum_{m in C_i^s} abar_km ) / d_i,
+ *   d_i = a_ii + sum_{n weak} a_in  (+ a_ik of strong F points k with an empty sum),
+ *   abar_km = a_km where its sign is opposite to a_kk's, else 0;
+ *   rows with |d_i| < CLASSICAL_GUARD a_ii (lumping cancelled the diagonal) take the
+ *   direct weights instead.
+ * interp = 1, direct interpolation for every row.
+ * C points interpolate by identity; F points without a strong C neighbour get an empty row. */
+#define CLASSICAL_GUARD 0.05
+static void build_interp(const ocsr* A, const ocsr* Sg, const int32_t* func, const int8_t* cf, int interp,
+                         ocsr* P, int64_t* ncoarse) {
   int64_t n = A->nrows;
   int64_t* cidx = xmalloc(n * sizeof(int64_t));
   int64_t nc = 0;
@@ -349,6 +391,8 @@ static void direct_interp(const ocsr* A, const ocsr* Sg, const int32_t* func, co
   P->ci = xmalloc(cap * sizeof(int32_t));
   P->v = xmalloc(cap * sizeof(double));
   int8_t* strong = xcalloc(n, 1);
+  int64_t* pos = xmalloc(n * sizeof(int64_t)); /* position of strong C point m in row i's P entries */
+  for (int64_t i = 0; i < n; ++i) pos[i] = -1;
   int64_t nnz = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (cf[i]) {
@@ -357,33 +401,54 @@ static void direct_interp(const ocsr* A, const ocsr* Sg, const int32_t* func, co
       continue;
     }
     int anyC = 0;
-    for (int64_t k = Sg->rp[i]; k < Sg->rp[i + 1]; ++k)
-      if (cf[Sg->ci[k]]) { strong[Sg->ci[k]] = 1; anyC = 1; }
-    if (anyC) {
-      double diag = 0.0, sn = 0.0, sp = 0.0, cn = 0.0, cp = 0.0;
-      for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+    for (int64_t k = Sg->rp[i]; k < Sg->rp[i + 1]; ++k) {
+      strong[Sg->ci[k]] = 1;
+      if (cf[Sg->ci[k]]) anyC = 1;
+    }
+    if (anyC && interp == 1) {
+      direct_row(A, i, func, strong, cidx, P, &nnz);
+    } else if (anyC) {
+      const int64_t row0 = nnz;
+      double diag = 0.0, aii = 0.0;
+      for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) { /* the strong C points, numerators a_ij */
         int64_t j = A->ci[k];
-        double a = A->v[k];
-        if (j == i) { diag = a; continue; }
+        if (j == i) { aii = A->v[k]; diag += A->v[k]; continue; }
         if (func[j] != func[i]) continue;
-        if (a < 0.0) sn += a; else sp += a;
-        if (strong[j]) { if (a < 0.0) cn += a; else cp += a; }
+        if (strong[j] && cf[j]) { P->ci[nnz] = (int32_t)cidx[j]; P->v[nnz] = A->v[k]; pos[j] = nnz; nnz++; }
       }
-      if (cp == 0.0) diag += sp;
-      double alpha = (cn != 0.0) ? sn / cn : 0.0;
-      double beta = (cp != 0.0) ? sp / cp : 0.0;
       for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
         int64_t j = A->ci[k];
-        if (j == i || !strong[j]) continue;
+        if (j == i || func[j] != func[i] || (strong[j] && cf[j])) continue;
         double a = A->v[k];
-        double w = (a < 0.0) ? -(alpha * a) / diag : -(beta * a) / diag;
-        P->ci[nnz] = (int32_t)cidx[j]; P->v[nnz] = w; nnz++;
+        if (!strong[j]) { diag += a; continue; } /* weak neighbour: lumped */
+        double akk = 0.0, den = 0.0;             /* strong F neighbour j: distributed over C_i^s */
+        for (int64_t q = A->rp[j]; q < A->rp[j + 1]; ++q) if (A->ci[q] == j) akk = A->v[q];
+        for (int64_t q = A->rp[j]; q < A->rp[j + 1]; ++q) {
+          int64_t m2 = A->ci[q];
+          if (m2 == j || pos[m2] < 0) continue;
+          double am = A->v[q];
+          if ((am < 0.0) != (akk < 0.0)) den += am;
+        }
+        if (den == 0.0) { diag += a; continue; }
+        for (int64_t q = A->rp[j]; q < A->rp[j + 1]; ++q) {
+          int64_t m2 = A->ci[q];
+          if (m2 == j || pos[m2] < 0) continue;
+          double am = A->v[q];
+          if ((am < 0.0) != (akk < 0.0)) P->v[pos[m2]] += a * am / den;
+        }
+      }
+      for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) pos[A->ci[k]] = -1;
+      if (fabs(diag) < CLASSICAL_GUARD * aii) {
+        nnz = row0;
+        direct_row(A, i, func, strong, cidx, P, &nnz);
+      } else {
+        for (int64_t q = row0; q < nnz; ++q) P->v[q] = -P->v[q] / diag;
       }
     }
     for (int64_t k = Sg->rp[i]; k < Sg->rp[i + 1]; ++k) strong[Sg->ci[k]] = 0;
     P->rp[i + 1] = nnz;
   }
-  free(strong); free(cidx);
+  free(strong); free(pos); free(cidx);
 }
 
 /* dense Cholesky (row-major lower); returns ORC_NOT_SPD on a non-positive pivot */
@@ -447,7 +512,7 @@ static int amg_setup(orc_t* h) {
     g->cf[l] = xmalloc(n);
     rs_coarsen(&Sg, g->cf[l]);
     int64_t nc = 0;
-    direct_interp(A, &Sg, g->func[l], g->cf[l], &g->P[l], &nc);
+    build_interp(A, &Sg, g->func[l], g->cf[l], o->interp, &g->P[l], &nc);
     csr_free(&Sg);
     if (nc == 0 || nc == n) { /* coarsening stalled: this level is the coarsest */
       csr_free(&g->P[l]); free(g->cf[l]); g->cf[l] = NULL;
@@ -660,7 +725,7 @@ static void filter_solve(orc_t* h, const double* v, double* w) {
 /* public API                                                          */
 
 void orc_opts_default(orc_opts* o) {
-  o->strength_theta = 0.8;
+  o->strength_theta = 0.55;
   o->max_coarse = 128;
   o->max_levels = 25;
   o->num_functions = 3;
@@ -668,6 +733,7 @@ void orc_opts_default(orc_opts* o) {
   o->filter = 1;
   o->contact_components = 0;
   o->build_amg = 1;
+  o->interp = 0;
 }
 
 const char* orc_error(orc_t* h) { return h ? h->err : "null handle"; }

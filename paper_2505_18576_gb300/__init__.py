@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("max_coarse", ctypes.c_int), ("num_functions", ctypes.c_int),
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int), ("contact_components", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("precision", ctypes.c_int), ("filter_algo", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("filter_algo", ctypes.c_int),
+                ("interp", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -201,9 +201,27 @@ struct Ctx {
 // groups widen until rows * K covers the resident threads (2048 per SM).
 static int lanes_for(int64_t rows, double avg_nnz, int num_sms) {
   int k = avg_nnz >= 6 ? 4 : 2;
+  if (avg_nnz >= 24) {
+    // level operators (FP64): group width by row count, from a sweep over the levels of
+    // 0.8-12 M-DOF hierarchies (narrow groups where the FP64 pipe binds, wide ones where
+    // too few rows are left to fill the GPU)
+    const int64_t sms = num_sms;
+    k = rows >= 1300 * sms ? 4 : (rows >= 80 * sms ? 8 : (rows >= 26 * sms ? 16 : 32));
+    while (k > 2 && k > avg_nnz) k /= 2;
+    return k;
+  }
   const double resident = 2048.0 * num_sms;
   while (k < 32 && (double)rows * k < resident && k < avg_nnz) k *= 2;
   return k;
+}
+
+// FP32 rows: memory-bound, so the group width follows the row length rather than the FP64
+// instruction count (measured on coarse levels of 0.2-6 M rows with 100-230 nonzeros per
+// row: 16 lanes 5.0-5.5 TB/s, 4 lanes 4.3-4.7 TB/s); small levels keep the latency rule.
+static int lanes_for_f32(int64_t rows, double avg_nnz, int num_sms) {
+  const int k = lanes_for(rows, avg_nnz, num_sms);
+  const int want = avg_nnz >= 48 ? 16 : (avg_nnz >= 12 ? 8 : k);
+  return want > k ? want : k;
 }
 
 static int grid_for(const Ctx& c, int64_t rows, int K) {
@@ -678,7 +696,7 @@ static int upload_csr_f(Ctx& c, const HCSR& h, DCSRf& d) {
   if ((st = c.upload(&d.ci, h.ci.data(), d.nnz))) return st;
   std::vector<float> v(h.v.begin(), h.v.end());
   if ((st = c.upload(&d.v, v.data(), d.nnz))) return st;
-  d.K = lanes_for(h.nrows, h.nrows ? (double)d.nnz / (double)h.nrows : 1.0, c.num_sms);
+  d.K = lanes_for_f32(h.nrows, h.nrows ? (double)d.nnz / (double)h.nrows : 1.0, c.num_sms);
   return AMGF_OK;
 }
 
@@ -953,7 +971,7 @@ extern "C" {
 int amgf_options_default(amgf_options* o) {
   if (!o) return fail(AMGF_ERR_INVALID_ARG, "null options");
   std::memset(o, 0, sizeof *o);
-  o->strength_theta = 0.8;
+  o->strength_theta = 0.55;
   o->rtol = 1e-8;
   o->max_levels = 25;
   o->max_coarse = 128;
@@ -966,6 +984,7 @@ int amgf_options_default(amgf_options* o) {
   o->verbose = 0;
   o->precision = 0;
   o->filter_algo = 0;
+  o->interp = 0;
   return AMGF_OK;
 }
 
@@ -990,7 +1009,8 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
   if (o) opt = *o; else amgf_options_default(&opt);
   if (opt.nu < 1 || opt.max_levels < 1 || opt.max_coarse < 1 || opt.num_functions < 1 || !(opt.rtol > 0.0) ||
       opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2 || opt.precision < 0 ||
-      opt.precision > 2 || opt.filter_algo < 0 || opt.filter_algo > 1)
+      opt.precision > 2 || opt.filter_algo < 0 || opt.filter_algo > 1 ||
+      opt.interp < 0 || opt.interp > 1)
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");

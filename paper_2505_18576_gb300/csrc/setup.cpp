@@ -7,13 +7,16 @@
 //   strength    j != i strong for i iff same unknown and |a_ij| >= theta * max_k |a_ik|
 //   coarsening  Ruge-Stueben first pass, largest measure first, ties to the smaller index,
 //               leftover points C if they have a strong influencer, else F
-//   interpolate direct interpolation with the sign split (Stueben), positive entries lumped
-//               into the diagonal when the row has no positive strong C neighbour
+//   interpolate classical (Ruge-Stueben) interpolation: strong F neighbours distributed over
+//               the row's strong C points, weak ones lumped into the diagonal; rows whose
+//               lumped diagonal nearly cancels (and interp = 1 for all rows) take direct
+//               interpolation with the sign split (Stueben)
 //   Galerkin    R = P^T, A_c = R (A P), sums in ascending index order
 //   smoother    l1-Jacobi, l1_i = sum_j |a_ij|
 // A_w = P^T A P = A[I_c, I_c] (Section 5.1) is ordered by reverse Cuthill-McKee from a
-// pseudo-peripheral vertex (George & Liu) and factored as a block-tridiagonal LDL^T whose
-// block size is the bandwidth, giving an exact solve with dense block operations.
+// pseudo-peripheral vertex (George & Liu), where it is block tridiagonal with the bandwidth
+// as block size, and prepared for an exact solve with dense block operations: odd-even
+// block cyclic reduction, or block LDL^T.
 #include "setup.h"
 
 #include <algorithm>
@@ -214,9 +217,16 @@ std::vector<int8_t> ruge_stueben(int64_t n, const std::vector<int64_t>& srp, con
   return cf;
 }
 
-// Direct interpolation with the sign split.
-HCSR direct_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const std::vector<int32_t>& sci,
-                          const std::vector<int32_t>& func, const std::vector<int8_t>& cf, int64_t& nc) {
+// Interpolation from the C/F split.  interp 0: classical (Ruge-Stueben) interpolation,
+//   w_ij = -(a_ij + sum_{k strong F} a_ik abar_kj / sum_{m strong C of i} abar_km) / d_i,
+//   abar_km = a_km when its sign is opposite to a_kk's (else 0), d_i = a_ii + weak entries
+//   (+ a_ik of strong F points with an empty sum); a row with |d_i| < 0.05 a_ii takes the
+//   direct weights.  interp 1: direct interpolation with the sign split for every row.
+// Same-function couplings only; every sum runs in ascending column order.
+constexpr double kClassicalGuard = 0.05;
+
+HCSR build_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const std::vector<int32_t>& sci,
+                         const std::vector<int32_t>& func, const std::vector<int8_t>& cf, int interp, int64_t& nc) {
   const int64_t n = A.nrows;
   std::vector<int64_t> cidx(n, -1);
   nc = 0;
@@ -230,12 +240,10 @@ HCSR direct_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const 
     auto& L = pc.len[t];
     auto& C = pc.ci[t];
     auto& V = pc.v[t];
-    for (int64_t i = bounds[t]; i < bounds[t + 1]; ++i) {
-      if (cf[i]) { L.push_back(1); C.push_back((int32_t)cidx[i]); V.push_back(1.0); continue; }
-      bool anyC = false;
-      for (int64_t k = srp[i]; k < srp[i + 1]; ++k) anyC |= cf[sci[k]] != 0;
-      if (!anyC) { L.push_back(0); continue; }
-      // walk row i of A and the (ascending) strong list together
+    std::vector<int32_t> ccol;  // strong C neighbours of the row (ascending) and their accumulators
+    std::vector<double> cval;
+    // direct interpolation weights of F row i (walks row i of A and the ascending strong list together)
+    auto direct_row = [&](int64_t i) {
       double diag = 0.0, sn = 0.0, sp = 0.0, cn = 0.0, cp = 0.0;
       int64_t s = srp[i];
       for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
@@ -265,6 +273,66 @@ HCSR direct_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const 
         ++cnt;
       }
       L.push_back(cnt);
+    };
+    for (int64_t i = bounds[t]; i < bounds[t + 1]; ++i) {
+      if (cf[i]) { L.push_back(1); C.push_back((int32_t)cidx[i]); V.push_back(1.0); continue; }
+      bool anyC = false;
+      for (int64_t k = srp[i]; k < srp[i + 1]; ++k) anyC |= cf[sci[k]] != 0;
+      if (!anyC) { L.push_back(0); continue; }
+      if (interp == 1) { direct_row(i); continue; }
+      // classical: numerators start at a_ij for the strong C neighbours
+      ccol.clear();
+      cval.clear();
+      double diag = 0.0, aii = 0.0;
+      int64_t s = srp[i];
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int32_t j = A.ci[k];
+        if (j == i) { aii = A.v[k]; diag += A.v[k]; continue; }
+        if (func[j] != func[i]) continue;
+        while (s < srp[i + 1] && sci[s] < j) ++s;
+        if (s < srp[i + 1] && sci[s] == j && cf[j]) { ccol.push_back(j); cval.push_back(A.v[k]); }
+      }
+      s = srp[i];
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        const int32_t j = A.ci[k];
+        if (j == i || func[j] != func[i]) continue;
+        while (s < srp[i + 1] && sci[s] < j) ++s;
+        const bool strong = s < srp[i + 1] && sci[s] == j;
+        if (strong && cf[j]) continue;
+        const double a = A.v[k];
+        if (!strong) { diag += a; continue; }  // weak neighbour: lumped
+        // strong F neighbour j: distributed over the strong C points of i through row j
+        double ajj = 0.0, den = 0.0;
+        for (int64_t q = A.rp[j]; q < A.rp[j + 1]; ++q)
+          if (A.ci[q] == j) ajj = A.v[q];
+        size_t c = 0;
+        for (int64_t q = A.rp[j]; q < A.rp[j + 1]; ++q) {
+          const int32_t m = A.ci[q];
+          if (m == j) continue;
+          while (c < ccol.size() && ccol[c] < m) ++c;
+          if (c == ccol.size()) break;
+          if (ccol[c] != m) continue;
+          const double am = A.v[q];
+          if ((am < 0.0) != (ajj < 0.0)) den += am;
+        }
+        if (den == 0.0) { diag += a; continue; }
+        c = 0;
+        for (int64_t q = A.rp[j]; q < A.rp[j + 1]; ++q) {
+          const int32_t m = A.ci[q];
+          if (m == j) continue;
+          while (c < ccol.size() && ccol[c] < m) ++c;
+          if (c == ccol.size()) break;
+          if (ccol[c] != m) continue;
+          const double am = A.v[q];
+          if ((am < 0.0) != (ajj < 0.0)) cval[c] += a * am / den;
+        }
+      }
+      if (std::fabs(diag) < kClassicalGuard * aii) { direct_row(i); continue; }
+      for (size_t c = 0; c < ccol.size(); ++c) {
+        C.push_back((int32_t)cidx[ccol[c]]);
+        V.push_back(-cval[c] / diag);
+      }
+      L.push_back((int64_t)ccol.size());
     }
   }
   HCSR P;
@@ -657,7 +725,7 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
     strength_graph(A, H.func[l], o.strength_theta, srp, sci);
     std::vector<int8_t> cf = ruge_stueben(n, srp, sci);
     int64_t nc = 0;
-    HCSR P = direct_interpolation(A, srp, sci, H.func[l], cf, nc);
+    HCSR P = build_interpolation(A, srp, sci, H.func[l], cf, o.interp, nc);
     if (nc == 0 || nc == n) break;  // coarsening stalled: this level is the coarsest
     HCSR R = transpose(P);
     HCSR AP = spgemm(A, P);

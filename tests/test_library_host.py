@@ -58,6 +58,8 @@ def test_host_setup_matches_oracle_bitwise(dims):
 
 def test_host_setup_matches_oracle_options(tiny):
     _compare_hierarchy(tiny, strength_theta=0.25)
+    _compare_hierarchy(tiny, interp=1)
+    _compare_hierarchy(tiny, interp=1, strength_theta=0.8)
     _compare_hierarchy(tiny, contact_components=1)
     _compare_hierarchy(tiny, max_coarse=400)
 

@@ -64,6 +64,44 @@ def test_rs_2d_3x3_hand_derived():
         assert np.allclose(P[int(row)], w, rtol=0, atol=1e-15)
 
 
+def _golden_matrix(g):
+    m = g["matrix"]
+    A = np.diag(np.asarray(m["diag"], float))
+    for i, j, a in m["offdiag"]:
+        A[i, j] = A[j, i] = a
+    return A
+
+
+def test_classical_interpolation_hand_derived():
+    # strong F-F couplings: classical weights differ from direct ones (golden/classical_6pt.json)
+    g = json.load(open(os.path.join(GOLDEN, "classical_6pt.json")))
+    A = _golden_matrix(g)
+    assert np.all(np.linalg.eigvalsh(A) > 0)
+    o = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=2, filter=0, strength_theta=0.5)
+    assert list(np.nonzero(o.cf(0))[0]) == g["C_points"]
+    P = o.P(0).toarray()
+    for row, w in g["P_rows"].items():
+        assert np.allclose(P[int(row)], w, rtol=0, atol=1e-15)
+    od = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=2, filter=0, strength_theta=0.5, interp=1)
+    Pd = od.P(0).toarray()
+    for row, w in g["P_rows_direct"].items():
+        assert np.allclose(Pd[int(row)], w, rtol=0, atol=1e-15)
+
+
+def test_classical_guard_falls_back_to_direct():
+    # a row whose lumped diagonal nearly cancels takes the direct weights
+    # (golden/classical_guard_10pt.json)
+    g = json.load(open(os.path.join(GOLDEN, "classical_guard_10pt.json")))
+    A = _golden_matrix(g)
+    assert np.all(np.linalg.eigvalsh(A) > 0)
+    o = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=3, filter=0, strength_theta=0.55)
+    assert list(np.nonzero(o.cf(0))[0]) == g["C_points"]
+    P = o.P(0).toarray()
+    assert np.all(np.isfinite(P))
+    for row, w in g["P_rows"].items():
+        assert np.allclose(P[int(row)], w, rtol=0, atol=1e-14)
+
+
 def test_rs_every_f_point_has_strong_c_neighbour():
     o = oracle.Oracle(csr_of(lap2d(17)), num_functions=1, max_coarse=10, filter=0, strength_theta=0.25)
     A = o.A(0)
@@ -89,13 +127,15 @@ def _zero_rowsum_matrix(n, seed):
     return (A + sp.diags(d)).tocsr()
 
 
+@pytest.mark.parametrize("interp", [0, 1])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_direct_interpolation_preserves_constants(seed):
-    # For zero row sums, direct interpolation with the sign split reproduces constants
-    # exactly on every F row that has a strong C neighbour (Stueben's construction).
+def test_interpolation_preserves_constants(seed, interp):
+    # For zero row sums, both classical interpolation (distributed strong F couplings, lumped
+    # weak ones) and direct interpolation with the sign split reproduce constants exactly on
+    # every F row that has a strong C neighbour (Ruge & Stueben's and Stueben's constructions).
     A = _zero_rowsum_matrix(400, seed)
     A = A + sp.identity(400) * 1e-12 * abs(A).max()
-    o = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=20, filter=0, strength_theta=0.25)
+    o = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=20, filter=0, strength_theta=0.25, interp=interp)
     P = o.P(0)
     s = P @ np.ones(P.shape[1])
     has = np.diff(P.indptr) > 0

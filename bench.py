@@ -258,9 +258,10 @@ def run_gpu(args, rank, world, local):
     if not args.no_variants:
         x_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
         s.pcg_solve(bdev[0], x_ref)
-        table = [("fp64", 0, False), ("fp32_vcycle", 1, False), ("fp32_vcycle_bf16_K", 2, False)]
+        table = [("fp64", 0, False), ("fp32_vcycle", 1, False), ("fp32_vcycle_bf16_K", 2, False),
+                 ("fp32_vcycle_bf16_all", 3, False)]
         if os.path.exists(WEIGHTS):
-            table.append(("fp32_vcycle_bf16_K_learned", 2, True))
+            table += [("fp32_vcycle_bf16_K_learned", 2, True), ("fp32_vcycle_bf16_all_learned", 3, True)]
         wanted = None if args.variants == "all" else set(args.variants.split(","))
         for name, prec, learned in table:
             if (prec, learned) == (args.precision, weights is not None) or (wanted and name not in wanted):
@@ -345,10 +346,11 @@ def run_gpu(args, rank, world, local):
         line = {
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32" + ("+bf16" if args.precision == 2 else ""),
+            "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32" + ("+bf16" if args.precision >= 2 else ""),
             "data": "synthetic",
             "config": {"workload": f"{args.config}: {WORKLOADS.get(args.config, args.config)}",
-                       "precision": ["fp64", "fp32 V-cycle", "fp32 V-cycle, bf16 fine K"][args.precision],
+                       "precision": ["fp64", "fp32 V-cycle", "fp32 V-cycle, bf16 fine K",
+                                     "fp32 V-cycle, bf16 storage of all V-cycle matrices"][args.precision],
                        "smoother": "l1-Jacobi, learned theta (MLP)" if weights is not None else "l1-Jacobi, theta = 1",
                        "n": n, "m": p.m, "nc": int(info.nc), "levels": int(info.nlevels),
                        "op_complexity": round(float(info.op_complexity), 4), "rtol": 1e-8,
@@ -402,12 +404,13 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations timed for cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=4, help="oracle PCG iterations per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
-                    help="V-cycle precision of the timed solve: 0 FP64, 1 FP32, 2 FP32 with BF16 fine-level K")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="V-cycle precision of the timed solve: 0 FP64, 1 FP32, 2 FP32 with BF16 fine-level K, "
+                         "3 FP32 arithmetic with BF16 storage of every V-cycle matrix")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant timings")
     ap.add_argument("--variants", default="all",
                     help="comma list of variants to time (fp64, fp32_vcycle, fp32_vcycle_bf16_K, "
-                         "fp32_vcycle_bf16_K_learned) or 'all'")
+                         "fp32_vcycle_bf16_all, fp32_vcycle_bf16_K_learned, fp32_vcycle_bf16_all_learned) or 'all'")
     ap.add_argument("--weights", default=None,
                     help="learned smoother weights (.npz) for the timed solve; 'default' = the packaged c64 weights")
     ap.add_argument("--no-graph", action="store_true",

@@ -72,6 +72,8 @@ typedef struct {
                              vectors, int32 indices, FP32 accumulation) inside an FP64 flexible PCG;
                              the outer residual, the dot products, the J^T D J term and the filter
                              solve stay FP64.  2: as 1 with the fine-level K values in BF16.
+                             3: as 2 with every V-cycle matrix (coarse A_l, P_l, R_l) in BF16
+                             (FP32 accumulation throughout).
                              Needs >= 2 levels and 3 unknowns per node, else FP64 is used. */
   int filter_algo;        /* exact solver of the block-tridiagonal A_w (Section 5.1 filter step; the
                              paper uses a sparse direct solver): 0 = odd-even block cyclic reduction,
@@ -105,7 +107,10 @@ typedef struct {
   int64_t filter_block;      /* block size of the block-tridiagonal A_w factor */
   int64_t filter_nblocks;
   double op_complexity;      /* sum nnz(A_l) / nnz(A_0) */
-  double t_setup_s;          /* host setup wall time */
+  double t_setup_s;          /* setup wall time (host setup and device upload) */
+  double t_assemble_s;       /* of which: assembling A */
+  double t_hierarchy_s;      /*           the AMG hierarchy */
+  double t_filter_s;         /*           I_c, ordering and the A_w factor */
 } amgf_info;
 
 typedef struct amgf_ctx* amgf_handle;
@@ -130,6 +135,23 @@ int amgf_setup_host(const amgf_csr* K, const amgf_csr* J, const double* D,
 /* New interior-point iterate: same K and J, new barrier diagonal D (host, length m).
  * Across IP iterations only D changes (Section 4); B := AMG(A) is rebuilt for the new A. */
 int amgf_update_D(amgf_handle h, const double* D);
+
+/* Bound-constrained variant (Section 3, remark on bound constraints): with the additional
+ * bounds d_lo <= u - u_* <= d_hi the condensed matrix becomes K + J~^T D~ J~ with
+ * J~ = [J; I; -I] and D~ = diag(D, D_lo, D_hi), i.e. A = K + J^T D J + diag(D_lo + D_hi).
+ * d_lower, d_upper: host arrays of n finite values >= 0 (either may be NULL = 0), copied.
+ * The diagonal term is added after J^T D J; the filter space stays the nonzero columns of
+ * J (the bound rows touch every DOF and are not filtered; they only add to A's diagonal,
+ * which AMG takes as part of A), and in mixed precision the term stays FP64 with the
+ * contact term.  host_only != 0 behaves as amgf_setup_host.  Errors as amgf_setup, plus
+ * AMGF_ERR_NONFINITE / AMGF_ERR_NOT_SPD for a non-finite / negative bound entry.  The paper
+ * gives no solver for this variant beyond the matrix; this entry applies AMGF to it. */
+int amgf_setup_bounds(const amgf_csr* K, const amgf_csr* J, const double* D, const double* d_lower,
+                      const double* d_upper, const amgf_options* o, int host_only, amgf_handle* out);
+
+/* New IP iterate of the bound-constrained variant: D (length m) and the bound barrier
+ * diagonals (length n, NULL = 0; both NULL removes the bound term); same K and J. */
+int amgf_update_bounds(amgf_handle h, const double* D, const double* d_lower, const double* d_upper);
 
 /* z_dev = M r_dev, one AMGF application (Definition "AMGF"): y1 = B r; r1 = r - A y1;
  * y2 = y1 + P A_w^{-1} P^T r1; r2 = r1 - A P (A_w^{-1} P^T r1); z = y2 + B r2.

@@ -58,6 +58,8 @@ def _load():
     lib.orc_opts_default.argtypes = [vp]
     lib.orc_create.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp]
     lib.orc_create.restype = i32
+    lib.orc_create_bounds.argtypes = [i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
+    lib.orc_create_bounds.restype = i32
     lib.orc_free.argtypes = [vp]
     lib.orc_error.argtypes = [vp]
     lib.orc_error.restype = ctypes.c_char_p
@@ -106,10 +108,11 @@ class Oracle:
     """AMGF (or plain AMG) preconditioner and PCG for A = K + J^T D J, on the CPU in FP64.
 
     K, J: (row_ptr int64, col_idx int32, val float64) host CSR triples (or objects
-    with those attributes); D: barrier diagonal of length m (m may be 0).
+    with those attributes); D: barrier diagonal of length m (m may be 0); E: optional
+    diagonal D_lo + D_hi of the bound-constraint variant (length n, >= 0), added to A.
     """
 
-    def __init__(self, K, J=None, D=None, **opts):
+    def __init__(self, K, J=None, D=None, E=None, **opts):
         lib = _load()
         self._lib = lib
         self._h = ctypes.c_void_p()
@@ -124,10 +127,11 @@ class Oracle:
         else:
             jrp = np.zeros(1, np.int64); jci = np.zeros(1, np.int32); jv = np.zeros(1); m = 0
             Dv = np.zeros(1)
-        self._keep = (rp, ci, v, jrp, jci, jv, Dv)
+        Ev = None if E is None else np.ascontiguousarray(E, np.float64)
+        self._keep = (rp, ci, v, jrp, jci, jv, Dv, Ev)
         self.opts = default_opts(**opts)
-        st = lib.orc_create(n, _p(rp), _p(ci), _p(v), m, _p(jrp), _p(jci), _p(jv), _p(Dv),
-                            ctypes.byref(self.opts), ctypes.byref(self._h))
+        st = lib.orc_create_bounds(n, _p(rp), _p(ci), _p(v), m, _p(jrp), _p(jci), _p(jv), _p(Dv),
+                                   None if Ev is None else _p(Ev), ctypes.byref(self.opts), ctypes.byref(self._h))
         if st != 0:
             msg = lib.orc_error(self._h).decode() if self._h else ""
             self.close()

@@ -672,7 +672,7 @@ static int filter_setup(orc_t* h) {
   h->bw = bw;
   /* band storage of the permuted matrix, lower part: Lb[i*(bw+1) + (i-j)] */
   int64_t W = bw + 1;
-  h->Lb = xcalloc(nc * W, sizeof(double));
+  h->Lb = xcalloc((size_t)(nc > 0 ? nc : 1) * (size_t)(W > 0 ? W : 1), sizeof(double));
   for (int64_t t = 0; t < nc; ++t)
     for (int64_t k = Aw.rp[t]; k < Aw.rp[t + 1]; ++k) {
       int64_t i = ipos[t], j = ipos[Aw.ci[k]];
@@ -738,11 +738,31 @@ void orc_opts_default(orc_opts* o) {
 
 const char* orc_error(orc_t* h) { return h ? h->err : "null handle"; }
 
+/* Bound-constrained variant (Remark on bound constraints, Section 3): with
+ * J~ = [J; I; -I] and D~ = diag(D, D_lo, D_hi) the matrix is K + J~^T D~ J~ =
+ * K + J^T D J + diag(D_lo + D_hi).  E = D_lo + D_hi (length n, entries >= 0, NULL = 0) is
+ * added to the diagonal after the J^T D J term.  The filter space stays the nonzero
+ * columns of J: the bound rows would make every DOF a "contact" DOF. */
+int orc_create_bounds(int64_t n,
+                      const int64_t* Krp, const int32_t* Kci, const double* Kv,
+                      int64_t m,
+                      const int64_t* Jrp, const int32_t* Jci, const double* Jv,
+                      const double* D, const double* E, const orc_opts* opts, orc_t** out);
+void orc_free(orc_t* h);
+
 int orc_create(int64_t n,
                const int64_t* Krp, const int32_t* Kci, const double* Kv,
                int64_t m,
                const int64_t* Jrp, const int32_t* Jci, const double* Jv,
                const double* D, const orc_opts* opts, orc_t** out) {
+  return orc_create_bounds(n, Krp, Kci, Kv, m, Jrp, Jci, Jv, D, NULL, opts, out);
+}
+
+int orc_create_bounds(int64_t n,
+                      const int64_t* Krp, const int32_t* Kci, const double* Kv,
+                      int64_t m,
+                      const int64_t* Jrp, const int32_t* Jci, const double* Jv,
+                      const double* D, const double* E, const orc_opts* opts, orc_t** out) {
   *out = NULL;
   if (n <= 0 || m < 0) return ORC_INVALID;
   orc_t* h = xcalloc(1, sizeof(orc_t));
@@ -751,6 +771,10 @@ int orc_create(int64_t n,
   for (int64_t r = 0; r < m; ++r)
     if (!isfinite(D[r])) { free(h); return ORC_NONFINITE; }
     else if (!(D[r] > 0.0)) { free(h); return ORC_NOT_SPD; }
+  if (E)
+    for (int64_t i = 0; i < n; ++i)
+      if (!isfinite(E[i])) { free(h); return ORC_NONFINITE; }
+      else if (E[i] < 0.0) { free(h); return ORC_NOT_SPD; }
   ocsr K = {n, n, (int64_t*)Krp, (int32_t*)Kci, (double*)Kv};
   ocsr J = {m, n, (int64_t*)Jrp, (int32_t*)Jci, (double*)Jv};
   /* per-DOF contact data for the learned smoother's features: (J^T D J)_aa and the flag */
@@ -768,6 +792,15 @@ int orc_create(int64_t n,
     h->S.rp = xmalloc((n + 1) * sizeof(int64_t)); memcpy(h->S.rp, Krp, (n + 1) * sizeof(int64_t));
     h->S.ci = xmalloc(nnz * sizeof(int32_t)); memcpy(h->S.ci, Kci, nnz * sizeof(int32_t));
     h->S.v = xmalloc(nnz * sizeof(double)); memcpy(h->S.v, Kv, nnz * sizeof(double));
+  }
+  if (E) {
+    for (int64_t i = 0; i < n; ++i) {
+      int found = 0;
+      for (int64_t k = h->S.rp[i]; k < h->S.rp[i + 1]; ++k)
+        if (h->S.ci[k] == i) { h->S.v[k] += E[i]; found = 1; }
+      if (!found && E[i] != 0.0) { orc_free(h); return ORC_INVALID; } /* K stores its diagonal */
+      h->dcontact[i] += E[i];
+    }
   }
   if (!h->o.build_amg) {
     for (int i = 0; i < 8; ++i) h->w[i] = xmalloc(n * sizeof(double));

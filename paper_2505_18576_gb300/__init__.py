@@ -21,9 +21,11 @@ from .build import LIB as _LIB_PATH, build as _build
 __all__ = ["AmgfError", "Options", "Stats", "Info", "Solver", "load_library", "amgf_options_default",
            "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec", "amgf_filter_solve",
            "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
-           "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED"]
+           "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED",
+           "amgf_setup_bounds", "amgf_update_bounds"]
 
-EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec",
+EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_setup_bounds", "amgf_update_D",
+            "amgf_update_bounds", "amgf_apply", "amgf_vcycle", "amgf_matvec",
             "amgf_filter_solve", "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host",
             "amgf_get_info",
             "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
@@ -65,7 +67,8 @@ class Info(ctypes.Structure):
                 ("level_rows", ctypes.c_int64 * 32), ("level_nnz", ctypes.c_int64 * 32),
                 ("interp_nnz", ctypes.c_int64 * 32), ("filter_block", ctypes.c_int64),
                 ("filter_nblocks", ctypes.c_int64), ("op_complexity", ctypes.c_double),
-                ("t_setup_s", ctypes.c_double)]
+                ("t_setup_s", ctypes.c_double), ("t_assemble_s", ctypes.c_double),
+                ("t_hierarchy_s", ctypes.c_double), ("t_filter_s", ctypes.c_double)]
 
 
 _lib = None
@@ -86,7 +89,9 @@ def load_library(build_if_missing: bool = True):
         "amgf_options_default": [vp],
         "amgf_setup": [vp, vp, vp, vp, vp],
         "amgf_setup_host": [vp, vp, vp, vp, vp],
+        "amgf_setup_bounds": [vp, vp, vp, vp, vp, vp, i32, vp],
         "amgf_update_D": [vp, vp],
+        "amgf_update_bounds": [vp, vp, vp, vp],
         "amgf_apply": [vp, vp, vp, vp],
         "amgf_vcycle": [vp, vp, vp, vp],
         "amgf_matvec": [vp, vp, vp, vp],
@@ -188,6 +193,32 @@ def amgf_setup(K, J=None, D=None, opts: Options | None = None, host_only: bool =
                           _ptr(d) if d is not None else None, ctypes.byref(opts) if opts else None,
                           ctypes.byref(h)))
     return h
+
+
+def amgf_setup_bounds(K, J, D, d_lower, d_upper, opts: Options | None = None, host_only: bool = False):
+    """Bound-constrained variant A = K + J^T D J + diag(d_lower + d_upper) -> handle."""
+    lib = load_library()
+    keep: list = []
+    k = _csr(K, keep)
+    j = _csr(J, keep) if J is not None else None
+    d = np.ascontiguousarray(D, dtype=np.float64) if D is not None else None
+    lo = np.ascontiguousarray(d_lower, dtype=np.float64) if d_lower is not None else None
+    hi = np.ascontiguousarray(d_upper, dtype=np.float64) if d_upper is not None else None
+    h = ctypes.c_void_p()
+    _check(lib.amgf_setup_bounds(ctypes.byref(k), ctypes.byref(j) if j is not None else None,
+                                 _ptr(d) if d is not None else None, _ptr(lo) if lo is not None else None,
+                                 _ptr(hi) if hi is not None else None, ctypes.byref(opts) if opts else None,
+                                 1 if host_only else 0, ctypes.byref(h)))
+    return h
+
+
+def amgf_update_bounds(h, D, d_lower, d_upper):
+    d = np.ascontiguousarray(D, dtype=np.float64) if D is not None else None
+    lo = np.ascontiguousarray(d_lower, dtype=np.float64) if d_lower is not None else None
+    hi = np.ascontiguousarray(d_upper, dtype=np.float64) if d_upper is not None else None
+    _check(load_library().amgf_update_bounds(h, _ptr(d) if d is not None else None,
+                                             _ptr(lo) if lo is not None else None,
+                                             _ptr(hi) if hi is not None else None))
 
 
 def amgf_update_D(h, D):
@@ -297,9 +328,12 @@ def amgf_destroy(h):
 class Solver:
     """Owns one handle.  K, J: CSR objects with row_ptr/col_idx/val (contactgen.CSR works)."""
 
-    def __init__(self, K, J=None, D=None, host_only=False, **opts):
+    def __init__(self, K, J=None, D=None, host_only=False, d_lower=None, d_upper=None, **opts):
         self.opts = amgf_options_default(**opts)
-        self.h = amgf_setup(K, J, D, self.opts, host_only=host_only)
+        if d_lower is not None or d_upper is not None:
+            self.h = amgf_setup_bounds(K, J, D, d_lower, d_upper, self.opts, host_only=host_only)
+        else:
+            self.h = amgf_setup(K, J, D, self.opts, host_only=host_only)
         self.info = amgf_get_info(self.h)
         self.n = int(self.info.n)
         self.nc = int(self.info.nc)
@@ -314,6 +348,10 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def update_bounds(self, D, d_lower, d_upper):
+        amgf_update_bounds(self.h, D, d_lower, d_upper)
+        self.info = amgf_get_info(self.h)
 
     def update_D(self, D):
         amgf_update_D(self.h, D)

@@ -39,11 +39,11 @@ constexpr int MAX_DOT_BLOCKS = 4096;
 //   RESID_W y = b - s, y2 = w2 * y     POST    y = x + w (b - s) [+ add]
 enum : int { M_SPMV = 0, M_SPMV_ADD = 1, M_RESID = 2, M_RESID_W = 3, M_POST = 4, M_SPMV_W = 5 };
 
-template <typename T>
+template <typename T, typename VT = T>
 struct CsrArgsT {
   const int64_t* __restrict__ rp;
   const int32_t* __restrict__ ci;
-  const T* __restrict__ v;
+  const VT* __restrict__ v;  // stored values (VT = T, or BF16 for an FP32 V-cycle)
   int64_t nrows;
   const int64_t* __restrict__ rows;  // optional row indirection (output row = rows[i])
   const T* x;           // gathered vector
@@ -117,8 +117,12 @@ __device__ __forceinline__ void grid_dot_finish(double local, double* partial, d
   }
 }
 
-template <typename T, int K, int MODE, bool DOT>
-__global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T> a) {
+__device__ __forceinline__ double load_val(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float load_val(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float load_val(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+template <typename T, int K, int MODE, bool DOT, typename VT = T>
+__global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T, VT> a) {
   static_assert(K >= 1 && K <= 32 && (K & (K - 1)) == 0, "K must be a power of two <= 32");
   const int lane_w = threadIdx.x & 31;
   const int sub = lane_w & (K - 1);
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T> a) {
           const int64_t k = kb + (int64_t)u * K;
           const bool ok = k < k1;
           jj[u] = ok ? __ldg(a.ci + k) : -1;
-          vv[u] = ok ? __ldg(a.v + k) : T(0);
+          vv[u] = ok ? (T)load_val(a.v + k) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)

@@ -752,7 +752,35 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
   return AMGF_OK;
 }
 
-void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, int64_t n,
+int add_diagonal(HCSR& A, const double* E, std::string& err) {
+  const int64_t n = A.nrows;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!std::isfinite(E[i])) { err = "bound diagonal has a non-finite entry"; return AMGF_ERR_NONFINITE; }
+    if (E[i] < 0.0) { err = "bound diagonal has a negative entry"; return AMGF_ERR_NOT_SPD; }
+  }
+  HCSR B;
+  B.nrows = A.nrows;
+  B.ncols = A.ncols;
+  B.rp.assign(n + 1, 0);
+  B.ci.reserve(A.ci.size() + n);
+  B.v.reserve(A.v.size() + n);
+  for (int64_t i = 0; i < n; ++i) {
+    bool done = E[i] == 0.0;
+    for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+      const int32_t j = A.ci[k];
+      if (!done && j > i) { B.ci.push_back((int32_t)i); B.v.push_back(E[i]); done = true; }
+      if (j == i) { B.ci.push_back(j); B.v.push_back(A.v[k] + E[i]); done = true; continue; }
+      B.ci.push_back(j);
+      B.v.push_back(A.v[k]);
+    }
+    if (!done) { B.ci.push_back((int32_t)i); B.v.push_back(E[i]); }
+    B.rp[i + 1] = (int64_t)B.ci.size();
+  }
+  A = std::move(B);
+  return AMGF_OK;
+}
+
+void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, const double* E, int64_t n,
                        std::vector<std::vector<float>>& feat) {
   const int nlev = H.nlev();
   feat.assign(nlev > 1 ? nlev - 1 : 0, std::vector<float>());
@@ -764,6 +792,8 @@ void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, i
         d[J->col_idx[k]] += J->val[k] * (D[r] * J->val[k]);
         if (J->val[k] != 0.0) flag[J->col_idx[k]] = 1;
       }
+  if (E)
+    for (int64_t i = 0; i < n; ++i) d[i] += E[i];
   for (int l = 0; l + 1 < nlev; ++l) {
     const HCSR& A = H.A[l];
     const int64_t nl = A.nrows;

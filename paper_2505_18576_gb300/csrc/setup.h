@@ -89,15 +89,21 @@ int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& 
 // added to K_ab after it.
 int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, std::string& err);
 
+// A += diag(E) (E finite, >= 0, length A.nrows): entries are added to stored diagonal
+// entries, and a diagonal entry is inserted (in column order) where a row has none and
+// E_i != 0.  The bound-constrained variant K + J^T D J + diag(D_lo + D_hi).
+int add_diagonal(HCSR& A, const double* E, std::string& err);
+
 // B := AMG(A): strength, Ruge-Stueben first pass, direct interpolation, Galerkin, l1 sums,
 // dense inverse of the coarsest level.
 int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::string& err);
 
 // Features of the learned smoother for every smoothed level (6 per row, row-major):
 //   log10(a_ii)/10, log10(l1_i)/10, a_ii/l1_i, contact flag, log10(1 + d_i)/10, l/(nlev-1),
-// with d = diag(J^T D J) and the flag (nonzero column of J) on the fine level, carried to a
+// with d = diag(J^T D J) (+ E, the bound-constraint diagonal, when given) and the flag
+// (nonzero column of J) on the fine level, carried to a
 // coarse row from the fine C point it comes from.
-void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, int64_t n,
+void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, const double* E, int64_t n,
                        std::vector<std::vector<float>>& feat);
 
 // I_c, A_w = A[I_c, I_c], reverse Cuthill-McKee order, and the exact solver of the

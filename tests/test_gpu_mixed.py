@@ -1,9 +1,10 @@
-"""Mixed precision (FP32 V-cycle, optional BF16 fine-level K) inside the FP64 flexible PCG.
+"""Mixed precision (FP32 V-cycle; BF16 fine-level K, or BF16 on every V-cycle matrix) inside
+the FP64 flexible PCG.
 
 The oracle is FP64 throughout; each mixed result is checked against it:
   - V-cycle: ||B32 r - B r|| / ||B r|| is of the order of the FP32 unit roundoff times the
-    hierarchy's amplification: asserted <= 1e-4 (FP32) and <= 5e-2 (BF16 K: 2^-9 relative
-    perturbation of every fine-level value).
+    hierarchy's amplification: asserted <= 1e-4 (FP32) and <= 5e-2 (BF16: 2^-9 relative
+    perturbation of every stored value).
   - PCG: converges to rtol 1e-8 and the solution's A-norm distance to the oracle's is at most
     max(4 rtol sqrt(kappa(MA)), 10 f): each solve's A-norm error is bounded by rtol sqrt(kappa)
     (factor 2 margin for the FP32 preconditioner's spectrum), and f is the FP64 rounding floor
@@ -41,7 +42,7 @@ def case(request):
     return request.param, p, oracle.Oracle(p.K, p.J, p.D)
 
 
-@pytest.mark.parametrize("precision,tol", [(1, 1e-4), (2, 5e-2)])
+@pytest.mark.parametrize("precision,tol", [(1, 1e-4), (2, 5e-2), (3, 5e-2)])
 def test_mixed_vcycle_close_to_fp64(case, precision, tol):
     import paper_2505_18576_gb300 as m
     name, p, o = case
@@ -57,7 +58,7 @@ def test_mixed_vcycle_close_to_fp64(case, precision, tol):
     s.close()
 
 
-@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("precision", [1, 2, 3])
 def test_mixed_pcg_against_fp64_oracle(case, precision):
     import paper_2505_18576_gb300 as m
     name, p, o = case
@@ -81,18 +82,23 @@ def test_mixed_pcg_against_fp64_oracle(case, precision):
     s.close()
 
 
-def test_mixed_apply_close_to_fp64(case):
+@pytest.mark.parametrize("precision", [1, 3])
+def test_mixed_apply_close_to_fp64(case, precision):
     import paper_2505_18576_gb300 as m
     name, p, o = case
-    s = m.Solver(p.K, p.J, p.D, precision=1)
+    s = m.Solver(p.K, p.J, p.D, precision=precision)
     r = np.random.default_rng(2).standard_normal(p.n)
     z = torch.empty(p.n, dtype=torch.float64, device="cuda")
     s.apply(dev(r), z)
     torch.cuda.synchronize()
     zo = o.apply(r)
     err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
-    print(f"{name}: mixed apply rel diff {err:.2e}")
-    assert err <= 1e-3
+    print(f"{name} precision {precision}: mixed apply rel diff {err:.2e}")
+    # FP32: the V-cycle's 1e-7 error, amplified by the filter step.  BF16 on every V-cycle
+    # matrix: the V-cycle differs by ~2e-3, and the filter correction A_w^{-1} P^T (r - A y1)
+    # responds to that error through contact rows with entries up to D_max, so the apply
+    # moves by up to ~10% while the preconditioner quality (PCG iterations, above) does not.
+    assert err <= (1e-3 if precision == 1 else 0.2)
     s.close()
 
 

@@ -109,8 +109,12 @@ def test_invalid_inputs(tiny):
         amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, nu=0)
     assert e.value.status == 1
     with pytest.raises(amgf.AmgfError) as e:
-        amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, precision=3)
+        amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, precision=4)
     assert e.value.status == 1
+    for bad_opt in (dict(filter_algo=2), dict(interp=2)):
+        with pytest.raises(amgf.AmgfError) as e:
+            amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, **bad_opt)
+        assert e.value.status == 1
 
 
 def test_update_D_host(tiny):
@@ -129,3 +133,25 @@ def test_device_setup_without_gpu_fails_loudly(tiny):
     with pytest.raises(amgf.AmgfError) as e:
         amgf.Solver(tiny.K, tiny.J, tiny.D)
     assert e.value.status == 6
+
+
+def test_host_setup_bounds_matches_oracle_bitwise(tiny):
+    rng = np.random.default_rng(7)
+    dlo, dhi = 10.0 ** rng.uniform(-3, 3, tiny.n), 10.0 ** rng.uniform(-3, 3, tiny.n)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, E=dlo + dhi)
+    s = amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, d_lower=dlo, d_upper=dhi)
+    assert s.info.nlevels == o.nlev
+    for l in range(o.nlev):
+        A1, A2 = o.A(l), s.export(0, l)
+        assert np.array_equal(A1.indptr, A2.indptr) and np.array_equal(A1.indices, A2.indices)
+        assert np.array_equal(A1.data, A2.data)
+    assert np.array_equal(o.Ic(), s.contact_set())
+    # removing the bound term restores the plain hierarchy
+    s.update_bounds(tiny.D, None, None)
+    o0 = oracle.Oracle(tiny.K, tiny.J, tiny.D)
+    assert np.array_equal(o0.A(1).data, s.export(0, 1).data)
+    bad = dlo.copy(); bad[0] = -1.0
+    with pytest.raises(amgf.AmgfError) as e:
+        amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, d_lower=bad)
+    assert e.value.status == 3
+    s.close()

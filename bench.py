@@ -386,11 +386,17 @@ def fp64_peak_tflops():
 
 
 def kernel_source_sha():
+    """Hash of the source the roofline kernels are built from: the fine-level BSR3 kernels
+    (FP64 and mixed) and the host code that lays their operator out.  DRAM traffic stored in
+    profiles/roofline_traffic.json is used only while this hash is unchanged."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("kernels.cuh", "amgf.cu"):
-        with open(os.path.join(ROOT, "paper_2505_18576_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2505_18576_gb300", "csrc")
+    k = open(os.path.join(csrc, "kernels.cuh")).read()
+    h.update(k[k.index("struct BsrArgs {"):k.index("// Coarsest-level solve out")].encode())
+    c = open(os.path.join(csrc, "setup.cpp")).read()
+    i = c.index("bool build_bsr3(")
+    h.update(c[i:c.index("\nint validate_csr(", i)].encode())
     return h.hexdigest()[:12]
 
 

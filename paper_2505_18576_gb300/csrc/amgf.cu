@@ -372,7 +372,7 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
     const int lc = nlev - 1;
     const double* rc = rhs_of(lc);
     double* oc = lc == 0 ? out0 : c.L[lc].out;
-    dense_gemv_kernel<<<1, TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, lc == 0 ? add0 : nullptr, oc,
+    dense_gemv_kernel<<<1, DENSE_TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, lc == 0 ? add0 : nullptr, oc,
                                           lc == 0 ? dotv : nullptr, lc == 0 ? dotres : nullptr);
     c.launches++;
   }
@@ -428,7 +428,7 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
       launch_csr_f<M_SPMV>(c, lv.Rf, rs);
     }
   }
-  dense_gemv_f32_kernel<<<1, TPB, 0, c.s>>>(c.nL, c.coarse_inv_f, c.L[nlev - 1].rhsf, c.L[nlev - 1].outf);
+  dense_gemv_f32_kernel<<<1, DENSE_TPB, 0, c.s>>>(c.nL, c.coarse_inv_f, c.L[nlev - 1].rhsf, c.L[nlev - 1].outf);
   c.launches++;
   for (int l = nlev - 2; l >= 0; --l) {
     DLevel& lv = c.L[l];
@@ -500,18 +500,23 @@ static void launch_sweep(Ctx& c, bool fwd, const double* M, const double* r, con
 static void enqueue_filter_solve_into(Ctx& c, const double* r, const double* vdirect, double* y, double* z, double* out) {
   const int64_t nb = c.F.nb, nblk = c.F.nblk;
   if (c.F.algo == 0) {  // block cyclic reduction: y holds the reduced right-hand sides
-    const int tiles = (int)((nb + FBCR_ROWS - 1) / FBCR_ROWS);
     const size_t smem = 2 * (size_t)nb * sizeof(double);
     const int nphase = (int)c.F.phase_off.size() - 1;
     for (int q = 0; q < nphase; ++q) {
       const int64_t t0 = c.F.phase_off[q], nt = c.F.phase_off[q + 1] - t0;
+      // few output blocks: a warp per row and 8 rows per CTA, so that enough SMs pull the matrices
+      const bool wide = nt * ((nb + 31) / 32) < 2 * (int64_t)c.num_sms;
+      const int rows = wide ? FBCR_TPB / 32 : FBCR_TPB / 8;
+      const int tiles = (int)((nb + rows - 1) / rows);
       const unsigned grid = (unsigned)(nt * tiles);
-      if (q == 0)
-        filter_bcr_kernel<true><<<grid, FBCR_TPB, smem, c.s>>>(c.ftasks + t0, tiles, c.fM, nb, r, c.fgidx, vdirect,
-                                                               c.F.nc, y, out);
-      else
-        filter_bcr_kernel<false><<<grid, FBCR_TPB, smem, c.s>>>(c.ftasks + t0, tiles, c.fM, nb, r, c.fgidx, vdirect,
-                                                                c.F.nc, y, out);
+      auto go = [&](auto kern) {
+        kern<<<grid, FBCR_TPB, smem, c.s>>>(c.ftasks + t0, tiles, c.fM, nb, r, c.fgidx, vdirect, c.F.nc, y, out);
+      };
+      if (q == 0) {
+        if (wide) go(filter_bcr_kernel<true, 32>); else go(filter_bcr_kernel<true, 8>);
+      } else {
+        if (wide) go(filter_bcr_kernel<false, 32>); else go(filter_bcr_kernel<false, 8>);
+      }
       c.launches++;
     }
     return;
@@ -886,12 +891,13 @@ static int build_all(Ctx& c, const double* D) {
       if ((st = c.upload(&c.fM, c.F.M.data(), (int64_t)c.F.M.size()))) return st;
       if ((st = c.upload(&c.ftasks, c.F.tasks.data(), (int64_t)c.F.tasks.size()))) return st;
       std::vector<double>().swap(c.F.M);  // the device copy is the only one used
-      if (2 * c.F.nb * (int64_t)sizeof(double) > 48 * 1024)
-        CK(cudaFuncSetAttribute(filter_bcr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * c.F.nb * sizeof(double))));
-      if (2 * c.F.nb * (int64_t)sizeof(double) > 48 * 1024)
-        CK(cudaFuncSetAttribute(filter_bcr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * c.F.nb * sizeof(double))));
+      if (2 * c.F.nb * (int64_t)sizeof(double) > 48 * 1024) {
+        const int bytes = (int)(2 * c.F.nb * sizeof(double));
+        CK(cudaFuncSetAttribute(filter_bcr_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        CK(cudaFuncSetAttribute(filter_bcr_kernel<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        CK(cudaFuncSetAttribute(filter_bcr_kernel<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        CK(cudaFuncSetAttribute(filter_bcr_kernel<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+      }
     } else {
       if ((st = c.upload(&c.fG, c.F.G.data(), tot * c.F.nb))) return st;
       if ((st = c.upload(&c.fGT, c.F.GT.data(), tot * c.F.nb))) return st;

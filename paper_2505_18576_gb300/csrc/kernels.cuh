@@ -327,7 +327,12 @@ __global__ void __launch_bounds__(TPB) bsr3_mixed_kernel(Bsr3MixedArgs<VT> a) {
 }
 
 // out = Ainv * r, single precision, one block (coarsest level of the FP32 V-cycle)
-__global__ void __launch_bounds__(TPB) dense_gemv_f32_kernel(int64_t n, const float* __restrict__ Ainv,
+// Coarsest-level solve out = A_L^{-1} r with the host-computed dense inverse: one CTA of
+// DENSE_TPB threads, a warp per row (the rows' loads are independent, so 32 warps keep
+// enough of them in flight; the solve is latency bound at n_L <= 128).
+constexpr int DENSE_TPB = 1024;
+
+__global__ void __launch_bounds__(DENSE_TPB) dense_gemv_f32_kernel(int64_t n, const float* __restrict__ Ainv,
                                                              const float* __restrict__ r, float* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int64_t i = warp; i < n; i += nw) {
@@ -368,10 +373,10 @@ __global__ void axpy_w_kernel(int64_t n, const double* __restrict__ winv, const 
 }
 
 // out = Ainv * r (+ add), Ainv dense n x n row-major; optional dot(dotv, out). One block.
-__global__ void __launch_bounds__(TPB) dense_gemv_kernel(int64_t n, const double* __restrict__ Ainv,
-                                                         const double* __restrict__ r, const double* add,
-                                                         double* out, const double* dotv, double* result) {
-  __shared__ double red[TPB / 32];
+__global__ void __launch_bounds__(DENSE_TPB) dense_gemv_kernel(int64_t n, const double* __restrict__ Ainv,
+                                                               const double* __restrict__ r, const double* add,
+                                                               double* out, const double* dotv, double* result) {
+  __shared__ double red[DENSE_TPB / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double dacc = 0.0;
   for (int64_t i = warp; i < n; i += nw) {
@@ -503,13 +508,17 @@ filter_sweep_kernel(bool fwd, const double* __restrict__ M, const int64_t* __res
 // coalesced) with two independent FMA chains.  GATHER: the phase reads the right-hand
 // side v straight from r[gidx[p]] (or vdirect[p]) in factor order, 0 on padding rows.
 constexpr int FBCR_TPB = 256;
-constexpr int FBCR_ROWS = FBCR_TPB / 8;
 
-template <bool GATHER>
+// LPR lanes reduce one row (8: 32 rows per CTA, for phases with many output blocks; 32: 8 rows
+// per CTA, four times the CTAs, for the few-block phases near the top of the reduction, which
+// are bound by how many loads are in flight rather than by the FP64 pipe).
+template <bool GATHER, int LPR>
 __global__ void __launch_bounds__(FBCR_TPB)
 filter_bcr_kernel(const FilterTask* __restrict__ tasks, int tiles, const double* __restrict__ M, int64_t nb,
                   const double* __restrict__ r, const int64_t* __restrict__ gidx, const double* __restrict__ vdirect,
                   int64_t nc, double* v, double* x) {
+  static_assert(LPR == 8 || LPR == 16 || LPR == 32, "lanes per row");
+  constexpr int ROWS = FBCR_TPB / LPR;
   extern __shared__ __align__(16) double fin[];  // [2][nb]: input blocks in0, in1
   const FilterTask t = tasks[blockIdx.x / tiles];
   const int64_t tile = blockIdx.x % tiles;
@@ -525,16 +534,16 @@ filter_bcr_kernel(const FilterTask* __restrict__ tasks, int tiles, const double*
   stage(t.in0, fin);
   stage(t.in1, fin + nb);
   __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 3, sub = lane & 7;
-  const int64_t row = tile * FBCR_ROWS + (threadIdx.x >> 5) * 4 + g;
+  const int sub = threadIdx.x & (LPR - 1);
+  const int64_t row = tile * ROWS + threadIdx.x / LPR;
   double sa = 0.0, sb = 0.0;
   auto term = [&](int64_t mat, int32_t blk, const double* xv) {
     if (mat < 0 || blk < 0) return;
     const double* mr = M + mat * nb * nb + row * nb;
     int64_t c = sub;
-    for (; c + 8 < nb; c += 16) {
+    for (; c + LPR < nb; c += 2 * LPR) {
       sa = fma(__ldg(mr + c), xv[c], sa);
-      sb = fma(__ldg(mr + c + 8), xv[c + 8], sb);
+      sb = fma(__ldg(mr + c + LPR), xv[c + LPR], sb);
     }
     if (c < nb) sa = fma(__ldg(mr + c), xv[c], sa);
   };
@@ -543,9 +552,8 @@ filter_bcr_kernel(const FilterTask* __restrict__ tasks, int tiles, const double*
     term(t.m1, t.in1, fin + nb);
   }
   double s = sa + sb;
-  s += __shfl_xor_sync(0xffffffffu, s, 4, 8);
-  s += __shfl_xor_sync(0xffffffffu, s, 2, 8);
-  s += __shfl_xor_sync(0xffffffffu, s, 1, 8);
+#pragma unroll
+  for (int off = LPR / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LPR);
   if (row < nb && sub == 0) {
     const int64_t p = (int64_t)t.out * nb + row;
     if (t.kind == 0) x[p] = s;

@@ -165,9 +165,10 @@ def solve(K, J, f, g0, tol: float = 1e-6, mu0: float = 1e-1, max_iter: int = 200
                    "active": int(np.sum(z > s))}  # complementarity: active where z dominates s
             if record_D:
                 rec["D"] = D.copy()
+                rec["b"] = b.copy()
             log.append(rec)
             if verbose:
-                print(json.dumps({k: v for k, v in rec.items() if k != "D"}), flush=True)
+                print(json.dumps({k: v for k, v in rec.items() if k not in ("D", "b")}), flush=True)
     finally:
         for sv in solvers.values():
             sv.close()
@@ -200,5 +201,5 @@ if __name__ == "__main__":
         np.savez(a.save_D, D=np.array([r["D"] for r in steps]))
     if a.json:
         with open(a.json, "w") as fh:
-            json.dump({"summary": summary, "steps": [{k: v for k, v in r.items() if k != "D"} for r in steps]}, fh,
+            json.dump({"summary": summary, "steps": [{k: v for k, v in r.items() if k not in ("D", "b")} for r in steps]}, fh,
                       indent=1)

@@ -1,5 +1,9 @@
 """Trainer driver of the learned l1-Jacobi smoother weights (not in the paper).
 
+Two training sets: the synthetic barrier sequence below (`run_experiment`), and the barrier
+diagonals of an actual interior-point run of the two-block contact QP (`run_ip_experiment`,
+ip.py), evaluated on the Newton systems of a run with another load.
+
 A small MLP (6 -> 32 -> 32 -> 1, ReLU) maps each row's features to a damping
 theta in [0.3, 1.2] of the l1-Jacobi step (W = theta / l1).  It is trained on the
 sequence of Schur complements A_k = K + J^T D_k J that an interior-point run produces:
@@ -97,6 +101,66 @@ def evaluate(K, J, barriers, b, weights, precision: int = 1, rtol: float = 1e-8)
     return out
 
 
+def evaluate_systems(K, J, systems, weights, precision: int = 1, rtol: float = 1e-8):
+    """Like evaluate, for a list of (D, b) pairs (each Newton system with its own right-hand side)."""
+    import torch
+    out = []
+    s = Solver(K, J, systems[0][0], precision=precision, rtol=rtol)
+    try:
+        x = torch.zeros(K.nrows, dtype=torch.float64, device="cuda")
+        for k, (D, b) in enumerate(systems):
+            if k > 0:
+                s.update_D(D)
+            bd = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+            s.set_mlp(None)
+            x.zero_()
+            st0 = s.pcg_solve(bd, x)
+            s.set_mlp(weights)
+            x.zero_()
+            st1 = s.pcg_solve(bd, x)
+            out.append({"system": k, "spread": float(D.max() / D.min()), "plain_iters": st0.iters,
+                        "learned_iters": st1.iters, "plain_s": st0.t_solve_s, "learned_s": st1.t_solve_s,
+                        "fallback": st1.mlp_fallback})
+            s.set_mlp(None)
+    finally:
+        s.close()
+    return out
+
+
+def run_ip_experiment(nx: int = 64, iters_per_system: int = 20, lr: float = 1e-3, seed: int = 0, precision: int = 1,
+                      train_load: float = 0.1, train_curvature: float = 0.2, eval_load: float = 0.15,
+                      eval_curvature: float = 0.3, out: str | None = None, verbose: bool = True) -> dict:
+    """Train on the barrier diagonals of an actual interior-point run (ip.py, the two-block
+    contact QP with one load) and evaluate on the Newton systems of a run with another load
+    and gap, each with its own right-hand side."""
+    from . import ip
+    K, J, f, g0 = ip.contact_qp(nx, load=train_load, curvature=train_curvature)
+    _, info = ip.solve(K, J, f, g0, record_D=True, precision=precision)
+    train_set = [(r["spread"], r["D"]) for r in info["steps"]]
+    _, _, f2, g2 = ip.contact_qp(nx, load=eval_load, curvature=eval_curvature)
+    _, info2 = ip.solve(K, J, f2, g2, record_D=True, precision=precision)
+    eval_sys = [(r["D"], r["b"]) for r in info2["steps"]]
+    t0 = time.perf_counter()
+    w, log = train(K, J, train_set, iters_per_system, lr, seed, verbose=verbose)
+    t_train = time.perf_counter() - t0
+    ev = evaluate_systems(K, J, eval_sys, w, precision=precision)
+    plain = sum(e["plain_iters"] for e in ev)
+    learned = sum(e["learned_iters"] for e in ev)
+    res = {"nx": nx, "train_systems": len(train_set), "eval_systems": len(eval_sys), "train_seconds": t_train,
+           "ip_iters_train": len(info["steps"]), "ip_iters_eval": len(info2["steps"]),
+           "plain_iters_total": plain, "learned_iters_total": learned,
+           "plain_s_total": sum(e["plain_s"] for e in ev), "learned_s_total": sum(e["learned_s"] for e in ev),
+           "decision": "learned" if learned < plain else "fallback: theta = 1", "eval": ev, "train_log": log}
+    if out:
+        unit = np.zeros(MLP_NW, np.float32)
+        unit[1312] = np.float32(np.log(3.5))
+        save_weights(out, w if learned < plain else unit, {"nx": nx, "source": "interior-point run",
+                                                            "decision": res["decision"]})
+    if verbose:
+        print(json.dumps({k: v for k, v in res.items() if k not in ("train_log", "eval")}), flush=True)
+    return res
+
+
 def save_weights(path: str, w, meta: dict | None = None):
     """Checkpoint: npz with the weights, a format version and free-form metadata."""
     np.savez(path, weights=np.asarray(w, np.float32), version=np.array([1]),
@@ -155,8 +219,14 @@ if __name__ == "__main__":
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--out", default=None)
     ap.add_argument("--json", default=None, help="write the full result (train log, per-system evaluation)")
+    ap.add_argument("--ip", action="store_true",
+                    help="train and evaluate on the Newton systems of interior-point runs (ip.py) instead")
+    ap.add_argument("--nx", type=int, default=64, help="elements per side for --ip")
     a = ap.parse_args()
-    r = run_experiment(a.config, a.train, a.eval, a.iters, a.lr, a.seed, a.precision, a.out)
+    if a.ip:
+        r = run_ip_experiment(a.nx, a.iters, a.lr, a.seed, a.precision, out=a.out)
+    else:
+        r = run_experiment(a.config, a.train, a.eval, a.iters, a.lr, a.seed, a.precision, a.out)
     if a.json:
         with open(a.json, "w") as f:
             json.dump(r, f, indent=1)

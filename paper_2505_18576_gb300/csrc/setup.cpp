@@ -20,6 +20,7 @@
 #include "setup.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -657,53 +658,84 @@ int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, s
         cval[p] = J->val[k];
       }
   }
-  const int parts = std::max(1, nthreads() * 4);
-  auto bounds = split_rows(n, parts);
-  RowPieces pc(parts);
+  // Rows without a contact column are copied from K; the (few) contact rows are merged.
+  // Two passes: row lengths, then values written in place.
+  std::vector<int64_t> crows;  // rows a with a nonzero column of J
+  for (int64_t a = 0; a < n; ++a)
+    if (crp[a + 1] > crp[a]) crows.push_back(a);
+  std::vector<std::vector<int32_t>> ccol(crows.size());
+  std::vector<std::vector<double>> cacc(crows.size());
 #pragma omp parallel
   {
     std::vector<double> acc(n, 0.0);
     std::vector<int64_t> mark(n, -1);
     std::vector<int32_t> cols;
-#pragma omp for schedule(dynamic, 1)
-    for (int t = 0; t < parts; ++t) {
-      for (int64_t a = bounds[t]; a < bounds[t + 1]; ++a) {
-        cols.clear();
-        for (int64_t k = crp[a]; k < crp[a + 1]; ++k) {
-          const int64_t r = crow[k];
-          const double jra = cval[k];
-          for (int64_t kk = J->row_ptr[r]; kk < J->row_ptr[r + 1]; ++kk) {
-            const int32_t b = J->col_idx[kk];
-            const double djrb = D[r] * J->val[kk];
-            if (mark[b] != a) { mark[b] = a; acc[b] = 0.0; cols.push_back(b); }
-            acc[b] += jra * djrb;
-          }
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t q = 0; q < (int64_t)crows.size(); ++q) {
+      const int64_t a = crows[q];
+      cols.clear();
+      for (int64_t k = crp[a]; k < crp[a + 1]; ++k) {
+        const int64_t r = crow[k];
+        const double jra = cval[k];
+        for (int64_t kk = J->row_ptr[r]; kk < J->row_ptr[r + 1]; ++kk) {
+          const int32_t b = J->col_idx[kk];
+          const double djrb = D[r] * J->val[kk];
+          if (mark[b] != a) { mark[b] = a; acc[b] = 0.0; cols.push_back(b); }
+          acc[b] += jra * djrb;
         }
-        std::sort(cols.begin(), cols.end());
-        // merge with row a of K (K value first, contact sum added to it)
-        int64_t p = K->row_ptr[a], pe = K->row_ptr[a + 1];
-        size_t q = 0;
-        int64_t cnt = 0;
-        while (p < pe || q < cols.size()) {
-          if (q >= cols.size() || (p < pe && K->col_idx[p] < cols[q])) {
-            pc.ci[t].push_back(K->col_idx[p]); pc.v[t].push_back(K->val[p]); ++p;
-          } else if (p >= pe || cols[q] < K->col_idx[p]) {
-            pc.ci[t].push_back(cols[q]); pc.v[t].push_back(acc[cols[q]]); ++q;
-          } else {
-            pc.ci[t].push_back(K->col_idx[p]); pc.v[t].push_back(K->val[p] + acc[cols[q]]); ++p; ++q;
-          }
-          ++cnt;
-        }
-        pc.len[t].push_back(cnt);
       }
+      std::sort(cols.begin(), cols.end());
+      ccol[q] = cols;
+      cacc[q].resize(cols.size());
+      for (size_t u = 0; u < cols.size(); ++u) cacc[q][u] = acc[cols[u]];
     }
   }
-  pc.gather(S, n, n);
+  // merge of row a of K with contact row q (K value first, contact sum added to it); emit(j, v)
+  auto merge = [&](int64_t a, int64_t q, auto&& emit) {
+    int64_t p = K->row_ptr[a], pe = K->row_ptr[a + 1];
+    const std::vector<int32_t>& cols = ccol[q];
+    size_t u = 0;
+    while (p < pe || u < cols.size()) {
+      if (u >= cols.size() || (p < pe && K->col_idx[p] < cols[u])) { emit(K->col_idx[p], K->val[p]); ++p; }
+      else if (p >= pe || cols[u] < K->col_idx[p]) { emit(cols[u], cacc[q][u]); ++u; }
+      else { emit(K->col_idx[p], K->val[p] + cacc[q][u]); ++p; ++u; }
+    }
+  };
+  std::vector<int64_t> qof(n, -1);
+  for (int64_t q = 0; q < (int64_t)crows.size(); ++q) qof[crows[q]] = q;
+  S.nrows = S.ncols = n;
+  S.rp.assign(n + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t a = 0; a < n; ++a) {
+    int64_t len = K->row_ptr[a + 1] - K->row_ptr[a];
+    if (qof[a] >= 0) {
+      len = 0;
+      merge(a, qof[a], [&](int32_t, double) { ++len; });
+    }
+    S.rp[a + 1] = len;
+  }
+  for (int64_t a = 0; a < n; ++a) S.rp[a + 1] += S.rp[a];
+  S.ci.resize(S.rp[n]);
+  S.v.resize(S.rp[n]);
+#pragma omp parallel for schedule(static)
+  for (int64_t a = 0; a < n; ++a) {
+    int64_t o = S.rp[a];
+    if (qof[a] < 0) {
+      std::copy(K->col_idx + K->row_ptr[a], K->col_idx + K->row_ptr[a + 1], S.ci.begin() + o);
+      std::copy(K->val + K->row_ptr[a], K->val + K->row_ptr[a + 1], S.v.begin() + o);
+    } else {
+      merge(a, qof[a], [&](int32_t j, double v) { S.ci[o] = j; S.v[o] = v; ++o; });
+    }
+  }
   return AMGF_OK;
 }
 
 int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::string& err) {
   H = Hierarchy();
+  double t_str = 0, t_rs = 0, t_int = 0, t_gal = 0;
+  auto now = [] {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  };
   H.A.push_back(S);
   H.func.emplace_back(S.nrows);
   for (int64_t i = 0; i < S.nrows; ++i) H.func[0][i] = o.num_functions > 1 ? (int32_t)(i % o.num_functions) : 0;
@@ -722,14 +754,20 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
     if (n <= o.max_coarse || l + 1 >= o.max_levels || l + 1 >= 32) break;
     std::vector<int64_t> srp;
     std::vector<int32_t> sci;
+    double t0 = now();
     strength_graph(A, H.func[l], o.strength_theta, srp, sci);
+    double t1 = now();
     std::vector<int8_t> cf = ruge_stueben(n, srp, sci);
+    double t2 = now();
     int64_t nc = 0;
     HCSR P = build_interpolation(A, srp, sci, H.func[l], cf, o.interp, nc);
+    double t3 = now();
+    t_str += t1 - t0; t_rs += t2 - t1; t_int += t3 - t2;
     if (nc == 0 || nc == n) break;  // coarsening stalled: this level is the coarsest
     HCSR R = transpose(P);
     HCSR AP = spgemm(A, P);
     HCSR Ac = spgemm(R, AP);
+    t_gal += now() - t3;
     H.cf.push_back(cf);
     std::vector<int32_t> fc;
     fc.reserve(nc);
@@ -741,6 +779,9 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
     H.func.push_back(std::move(fc));
     ++l;
   }
+  if (o.verbose)
+    fprintf(stderr, "amgf: hierarchy: strength %.2fs, coarsening %.2fs, interpolation %.2fs, Galerkin %.2fs\n", t_str,
+            t_rs, t_int, t_gal);
   const HCSR& AL = H.A.back();
   const int64_t nL = AL.nrows;
   if (nL > 8192) { err = "coarsest level too large for a dense solve"; return AMGF_ERR_INVALID_ARG; }

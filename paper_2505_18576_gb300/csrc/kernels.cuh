@@ -121,7 +121,7 @@ __device__ __forceinline__ double load_val(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float load_val(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float load_val(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 
-template <typename T, int K, int MODE, bool DOT, typename VT = T>
+template <typename T, int K, int MODE, bool DOT, typename VT = T, int U = 4>
 __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T, VT> a) {
   static_assert(K >= 1 && K <= 32 && (K & (K - 1)) == 0, "K must be a power of two <= 32");
   const int lane_w = threadIdx.x & 31;
@@ -138,7 +138,6 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T, VT> a) {
       const int64_t k1 = a.rp[i + 1];
       // batches of U entries per lane: all index/value loads of a batch are issued before
       // the dependent gathers, so each batch costs two memory round trips
-      constexpr int U = 4;
       for (int64_t kb = a.rp[i] + sub; kb < k1; kb += U * K) {
         int32_t jj[U];
         T vv[U];

@@ -326,3 +326,27 @@ def test_nonfinite_rhs_reports_status(tiny):
     x = torch.zeros(tiny.n, dtype=torch.float64, device="cuda")
     st = s.pcg_solve(dev(b), x, check=False)
     assert st.status == 2
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 1), (3, 2, 1), (4, 3, 2)])
+def test_filter_solve_few_blocks(dims):
+    # one, two and three diagonal blocks: cyclic reduction with 0, 1 and 2 reduction levels
+    import paper_2505_18576_gb300 as m
+    p = cg.make_problem(None, seed=4, nx=dims[0], ny=dims[1], nz=dims[2], d_lo=-2, d_hi=6)
+    o = oracle.Oracle(p.K, p.J, p.D)
+    kap, Aw = kappa_Aw(o)
+    for algo in (0, 1):
+        s = m.Solver(p.K, p.J, p.D, filter_algo=algo)
+        v = np.random.default_rng(5).standard_normal(o.nc)
+        w = torch.empty(o.nc, dtype=torch.float64, device="cuda")
+        s.filter_solve(dev(v), w)
+        wg = host(w)
+        assert np.linalg.norm(Aw @ wg - v) <= 64 * EPS * np.linalg.norm(Aw, 2) * np.linalg.norm(wg)
+        assert np.linalg.norm(wg - o.filter_solve(v)) <= max(1e-12, 16 * EPS * kap) * np.linalg.norm(wg)
+        # one or two AMG levels (on one level the coarsest solve is the dense inverse of A)
+        x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        st = s.pcg_solve(dev(p.b), x)
+        xo, ko, *_ = o.pcg(p.b, tol=1e-8)
+        assert st.converged == 1 and abs(st.iters - ko) <= 1
+        assert np.linalg.norm(host(x) - xo) <= 1e-8 * np.linalg.norm(xo)
+        s.close()

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(DENSE_TPB) dense_gemv_kernel(int64_t n, const 
   }
 }
 
-// ---------------- filter: A_w^{-1} via block LDL^T (block-tridiagonal A_w) ----------------
+// ---------------- filter: A_w^{-1} of the block-tridiagonal A_w ----------------
 
 constexpr int FILTER_TPB = 512;
 

@@ -136,6 +136,18 @@ int amgf_setup_host(const amgf_csr* K, const amgf_csr* J, const double* D,
  * Across IP iterations only D changes (Section 4); B := AMG(A) is rebuilt for the new A. */
 int amgf_update_D(amgf_handle h, const double* D);
 
+/* New IP iterate reusing the coarsening and interpolation of the last full setup (not in the
+ * paper, which rebuilds B := AMG(A) for every A): A = K + J^T D J, the filter A_w and the
+ * fine-level smoother weights are recomputed for the new D (host, length m), and every coarse
+ * operator is brought up to date by the Galerkin product of the change of the contact term,
+ * A_{l+1} += R_l dA_l P_l with dA_0 = J^T diag(D_new - D_old) J, so A_l = R ... A P ... for
+ * the old P_l.  B therefore stays the V-cycle of a Galerkin hierarchy of the current A (and
+ * M stays SPD, lambda_max(B A) <= 1); only its interpolation is from an earlier A, so PCG may
+ * need more iterations.  Skips strength, coarsening, interpolation and the full Galerkin
+ * products (most of the setup time).  Falls back to amgf_update_D when the hierarchy has one
+ * level or an update would leave a coarse pattern.  Errors as amgf_update_D. */
+int amgf_update_D_fine(amgf_handle h, const double* D);
+
 /* Bound-constrained variant (Section 3, remark on bound constraints): with the additional
  * bounds d_lo <= u - u_* <= d_hi the condensed matrix becomes K + J~^T D~ J~ with
  * J~ = [J; I; -I] and D~ = diag(D, D_lo, D_hi), i.e. A = K + J^T D J + diag(D_lo + D_hi).

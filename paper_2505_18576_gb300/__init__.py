@@ -22,10 +22,10 @@ __all__ = ["AmgfError", "Options", "Stats", "Info", "Solver", "load_library", "a
            "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec", "amgf_filter_solve",
            "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
            "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED",
-           "amgf_setup_bounds", "amgf_update_bounds"]
+           "amgf_setup_bounds", "amgf_update_bounds", "amgf_update_D_fine"]
 
 EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_setup_bounds", "amgf_update_D",
-            "amgf_update_bounds", "amgf_apply", "amgf_vcycle", "amgf_matvec",
+            "amgf_update_bounds", "amgf_update_D_fine", "amgf_apply", "amgf_vcycle", "amgf_matvec",
             "amgf_filter_solve", "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host",
             "amgf_get_info",
             "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
@@ -92,6 +92,7 @@ def load_library(build_if_missing: bool = True):
         "amgf_setup_bounds": [vp, vp, vp, vp, vp, vp, i32, vp],
         "amgf_update_D": [vp, vp],
         "amgf_update_bounds": [vp, vp, vp, vp],
+        "amgf_update_D_fine": [vp, vp],
         "amgf_apply": [vp, vp, vp, vp],
         "amgf_vcycle": [vp, vp, vp, vp],
         "amgf_matvec": [vp, vp, vp, vp],
@@ -219,6 +220,12 @@ def amgf_update_bounds(h, D, d_lower, d_upper):
     _check(load_library().amgf_update_bounds(h, _ptr(d) if d is not None else None,
                                              _ptr(lo) if lo is not None else None,
                                              _ptr(hi) if hi is not None else None))
+
+
+def amgf_update_D_fine(h, D):
+    """New D with the coarse levels of B kept from the last full setup (lagged hierarchy)."""
+    d = np.ascontiguousarray(D, dtype=np.float64)
+    _check(load_library().amgf_update_D_fine(h, _ptr(d)))
 
 
 def amgf_update_D(h, D):
@@ -353,8 +360,8 @@ class Solver:
         amgf_update_bounds(self.h, D, d_lower, d_upper)
         self.info = amgf_get_info(self.h)
 
-    def update_D(self, D):
-        amgf_update_D(self.h, D)
+    def update_D(self, D, keep_coarse: bool = False):
+        (amgf_update_D_fine if keep_coarse else amgf_update_D)(self.h, D)
         self.info = amgf_get_info(self.h)
 
     def apply(self, r, z, stream=None):

@@ -93,6 +93,7 @@ struct Ctx {
   // host copies kept for amgf_update_D and exports
   HCSR Kh, Jh;
   std::vector<double> Eh;  // bound-constraint diagonal D_lo + D_hi (empty: none)
+  std::vector<double> Dh;  // D of the current A (for amgf_update_D_fine)
   Hierarchy H;
   Filter F;
   amgf_info info{};
@@ -760,7 +761,9 @@ static void fill_info(Ctx& c) {
   in.filter_nblocks = c.F.nblk;
 }
 
-static int build_all(Ctx& c, const double* D) {
+// keep_coarse: new fine-level operator (and filter) for D, coarse levels of B kept from the
+// last full setup (amgf_update_D_fine)
+static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   auto t_start = std::chrono::steady_clock::now();
   std::string err;
   amgf_csr K{c.Kh.nrows, c.Kh.ncols, c.Kh.nnz(), c.Kh.rp.data(), c.Kh.ci.data(), c.Kh.v.data()};
@@ -775,8 +778,19 @@ static int build_all(Ctx& c, const double* D) {
   if (E && (st = add_diagonal(S, E, err))) return fail(st, err);
   const double t_assemble = since(t_start);
   auto t1 = std::chrono::steady_clock::now();
-  st = build_hierarchy(S, c.o, c.H, err);
-  if (st) return fail(st, err);
+  bool rebuilt = true;
+  if (keep_coarse && c.H.nlev() >= 2 && c.H.A[0].nrows == S.nrows && (int64_t)c.Dh.size() == c.m) {
+    std::vector<double> dD(c.m);
+    for (int64_t r = 0; r < c.m; ++r) dD[r] = D[r] - c.Dh[r];
+    st = update_hierarchy_contact(c.H, S, c.m > 0 ? &J : nullptr, dD.data(), err);
+    if (st == AMGF_ERR_NOT_SPD) return fail(st, err);
+    rebuilt = st != AMGF_OK;  // pattern mismatch: rebuild below
+  }
+  if (rebuilt) {
+    st = build_hierarchy(S, c.o, c.H, err);
+    if (st) return fail(st, err);
+  }
+  if (c.m > 0) c.Dh.assign(D, D + c.m);
   const double t_hier = since(t1);
   t1 = std::chrono::steady_clock::now();
   if (c.o.filter) {
@@ -1139,6 +1153,15 @@ int amgf_update_D(amgf_handle h, const double* D) {
   if (h->c.m > 0 && !D) return fail(AMGF_ERR_INVALID_ARG, "null D");
   if (!h->c.host_only) CK(cudaSetDevice(h->c.device));
   const int st = build_all(h->c, D);
+  if (st || h->c.host_only || h->c.mlp_w_host.empty()) return st;
+  return apply_smoother_weights(h->c, false);
+}
+
+int amgf_update_D_fine(amgf_handle h, const double* D) {
+  if (!h) return fail(AMGF_ERR_INVALID_ARG, "null handle");
+  if (h->c.m > 0 && !D) return fail(AMGF_ERR_INVALID_ARG, "null D");
+  if (!h->c.host_only) CK(cudaSetDevice(h->c.device));
+  const int st = build_all(h->c, D, true);
   if (st || h->c.host_only || h->c.mlp_w_host.empty()) return st;
   return apply_smoother_weights(h->c, false);
 }

@@ -793,6 +793,56 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
   return AMGF_OK;
 }
 
+int update_hierarchy_contact(Hierarchy& H, const HCSR& S, const amgf_csr* J, const double* dD, std::string& err) {
+  const int nlev = H.nlev();
+  H.A[0] = S;
+  if (J && J->nrows > 0 && nlev >= 2) {
+    // dA_0 = J^T diag(dD) J
+    HCSR Jh;
+    Jh.nrows = J->nrows;
+    Jh.ncols = J->ncols;
+    Jh.rp.assign(J->row_ptr, J->row_ptr + J->nrows + 1);
+    Jh.ci.assign(J->col_idx, J->col_idx + J->nnz);
+    Jh.v.assign(J->val, J->val + J->nnz);
+    HCSR DJ = Jh;
+    for (int64_t r = 0; r < Jh.nrows; ++r)
+      for (int64_t k = Jh.rp[r]; k < Jh.rp[r + 1]; ++k) DJ.v[k] = dD[r] * Jh.v[k];
+    HCSR dA = spgemm(transpose(Jh), DJ);
+    for (int l = 0; l + 1 < nlev; ++l) {
+      HCSR dAc = spgemm(H.R[l], spgemm(dA, H.P[l]));
+      HCSR& Ac = H.A[l + 1];
+      bool ok = true;
+#pragma omp parallel for schedule(dynamic, 256) reduction(&& : ok)
+      for (int64_t i = 0; i < dAc.nrows; ++i) {
+        int64_t p = Ac.rp[i];
+        for (int64_t k = dAc.rp[i]; k < dAc.rp[i + 1]; ++k) {
+          while (p < Ac.rp[i + 1] && Ac.ci[p] < dAc.ci[k]) ++p;
+          if (p == Ac.rp[i + 1] || Ac.ci[p] != dAc.ci[k]) { ok = false; break; }
+          Ac.v[p] += dAc.v[k];
+        }
+      }
+      if (!ok) { err = "contact update outside the coarse pattern"; return AMGF_ERR_INVALID_ARG; }
+      dA = std::move(dAc);
+    }
+  }
+  for (int l = 0; l < nlev; ++l) {
+    const HCSR& A = H.A[l];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < A.nrows; ++i) {
+      double a = 0.0;
+      for (int64_t k = A.rp[i]; k < A.rp[i + 1]; ++k) a += std::fabs(A.v[k]);
+      H.l1[l][i] = a;
+    }
+  }
+  const HCSR& AL = H.A.back();
+  const int64_t nL = AL.nrows;
+  std::vector<double> dense(nL * nL, 0.0);
+  for (int64_t i = 0; i < nL; ++i)
+    for (int64_t k = AL.rp[i]; k < AL.rp[i + 1]; ++k) dense[i * nL + AL.ci[k]] = AL.v[k];
+  if (!spd_inverse(dense, nL, H.coarse_inv)) { err = "coarsest matrix is not SPD"; return AMGF_ERR_NOT_SPD; }
+  return AMGF_OK;
+}
+
 int add_diagonal(HCSR& A, const double* E, std::string& err) {
   const int64_t n = A.nrows;
   for (int64_t i = 0; i < n; ++i) {

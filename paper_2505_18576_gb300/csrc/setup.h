@@ -89,6 +89,12 @@ int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& 
 // added to K_ab after it.
 int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, std::string& err);
 
+// New contact term for a hierarchy built earlier (interpolation reused): A_0 = S and
+// A_{l+1} += R_l dA_l P_l with dA_0 = J^T diag(dD) J, dD = D_new - D_old, so that every A_l is
+// again the Galerkin operator of the new A for the old P; l1 sums and the coarsest inverse
+// are recomputed.  AMGF_ERR_INVALID_ARG if an update falls outside a coarse pattern.
+int update_hierarchy_contact(Hierarchy& H, const HCSR& S, const amgf_csr* J, const double* dD, std::string& err);
+
 // A += diag(E) (E finite, >= 0, length A.nrows): entries are added to stored diagonal
 // entries, and a diagonal entry is inserted (in column order) where a row has none and
 // E_i != 0.  The bound-constrained variant K + J^T D J + diag(D_lo + D_hi).

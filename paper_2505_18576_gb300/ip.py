@@ -81,8 +81,8 @@ class GpuSolver:
         self.b = torch.zeros(K.nrows, dtype=torch.float64, device="cuda")
         self.x = torch.zeros(K.nrows, dtype=torch.float64, device="cuda")
 
-    def update_D(self, D):
-        self.s.update_D(D)
+    def update_D(self, D, keep_coarse: bool = False):
+        self.s.update_D(D, keep_coarse=keep_coarse)
 
     def solve(self, b):
         self.b.copy_(self.torch.from_numpy(np.ascontiguousarray(b)))
@@ -96,11 +96,15 @@ class GpuSolver:
 
 def solve(K, J, f, g0, tol: float = 1e-6, mu0: float = 1e-1, max_iter: int = 200, precision: int = 0,
           policy: str = "amgf", switch_spread: float = 1e6, weights=None, rtol: float = 1e-8,
-          verbose: bool = False, record_D: bool = False, make_solver=None):
+          verbose: bool = False, record_D: bool = False, make_solver=None, lag: float | None = None):
     """Run the IP loop; returns (u, info) with one record per Newton step in info["steps"].
 
-    make_solver(D, use_filter) -> object with update_D(D), solve(b) -> (x, iters, seconds) and
-    close(); default: GpuSolver (the library's AMGF-PCG on the current CUDA device)."""
+    make_solver(D, use_filter) -> object with update_D(D, keep_coarse), solve(b) -> (x, iters,
+    seconds) and close(); default: GpuSolver (the library's AMGF-PCG on the current CUDA device).
+    lag: None rebuilds the AMG hierarchy for every Newton system (B := AMG(A)); a number keeps
+    the coarse levels of the last full setup (amgf_update_D_fine: new fine-level operator and
+    filter only) until a solve needs more than (1 + lag) times the PCG iterations of the first
+    solve after that setup."""
     if make_solver is None:
         def make_solver(D, use_filter):
             return GpuSolver(K, J, D, use_filter, precision=precision, rtol=rtol, weights=weights)
@@ -122,6 +126,8 @@ def solve(K, J, f, g0, tol: float = 1e-6, mu0: float = 1e-1, max_iter: int = 200
         return max(np.abs(r_u).max() / fs, np.abs(r_s).max() / fs, np.abs(r_l).max() / gs,
                    np.abs(r_z).max() / (fs * gs))
     solvers = {}
+    base_iters = {}  # PCG iterations of the first solve after each solver's last full setup
+    full_next = {}
     log = []
     e0 = np.inf
     t_start = time.perf_counter()
@@ -144,12 +150,18 @@ def solve(K, J, f, g0, tol: float = 1e-6, mu0: float = 1e-1, max_iter: int = 200
             b = -r_u - Jsp.T @ (D * r_l + r_s + r_z / s)
             key = 1 if use_filter else 0
             t0 = time.perf_counter()
+            lagged = False
             if key not in solvers:
                 solvers[key] = make_solver(D, bool(key))
+                full_next[key] = True
             else:
-                solvers[key].update_D(D)
+                lagged = lag is not None and not full_next.get(key, True)
+                solvers[key].update_D(D, keep_coarse=lagged)
             t_setup = time.perf_counter() - t0
             du, kits, tsol = solvers[key].solve(b)
+            if not lagged:
+                base_iters[key] = kits
+            full_next[key] = lag is None or kits > (1.0 + lag) * base_iters[key]
             ds = Jsp @ du + r_l
             dz = -(r_z + z * ds) / s
             dl = r_s - dz
@@ -161,7 +173,7 @@ def solve(K, J, f, g0, tol: float = 1e-6, mu0: float = 1e-1, max_iter: int = 200
             z += ad * dz
             rec = {"iter": it, "mu": mu / (fs * gs), "e_opt": float(e0), "D_min": float(D.min()), "D_max": float(D.max()),
                    "spread": spread, "preconditioner": "amgf" if use_filter else "amg", "pcg_iters": kits,
-                   "solve_s": tsol, "setup_s": t_setup, "alpha_p": ap, "alpha_d": ad,
+                   "solve_s": tsol, "setup_s": t_setup, "lagged_setup": lagged, "alpha_p": ap, "alpha_d": ad,
                    "active": int(np.sum(z > s))}  # complementarity: active where z dominates s
             if record_D:
                 rec["D"] = D.copy()
@@ -184,14 +196,17 @@ if __name__ == "__main__":
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--policy", default="amgf", choices=["amgf", "amg", "switch"])
     ap.add_argument("--switch-spread", type=float, default=1e6)
+    ap.add_argument("--lag", type=float, default=None,
+                    help="keep the coarse levels while PCG iterations stay within (1 + lag) of the last full setup's")
     ap.add_argument("--save-D", default=None, help="write the IP sequence of D to this .npz")
     ap.add_argument("--json", default=None)
     a = ap.parse_args()
     K, J, f, g0 = contact_qp(a.nx)
     u, info = solve(K, J, f, g0, tol=a.tol, precision=a.precision, policy=a.policy, switch_spread=a.switch_spread,
-                    verbose=True, record_D=a.save_D is not None)
+                    verbose=True, record_D=a.save_D is not None, lag=a.lag)
     steps = info["steps"]
-    summary = {"nx": a.nx, "n": K.nrows, "m": J.nrows, "policy": a.policy, "ip_iters": len(steps),
+    summary = {"nx": a.nx, "n": K.nrows, "m": J.nrows, "policy": a.policy, "lag": a.lag, "ip_iters": len(steps),
+               "full_setups": sum(1 for r in steps if not r["lagged_setup"]),
                "converged": info["converged"], "final_e_opt": info["final_e_opt"],
                "pcg_iters_total": sum(r["pcg_iters"] for r in steps),
                "solve_s_total": sum(r["solve_s"] for r in steps), "setup_s_total": sum(r["setup_s"] for r in steps),

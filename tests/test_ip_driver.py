@@ -20,7 +20,7 @@ class OracleSolver:
         self.K, self.J, self.filter = K, J, 1 if use_filter else 0
         self.o = oracle.Oracle(K, J, D, filter=self.filter)
 
-    def update_D(self, D):
+    def update_D(self, D, keep_coarse=False):
         self.o.close()
         self.o = oracle.Oracle(self.K, self.J, D, filter=self.filter)
 

@@ -155,3 +155,21 @@ def test_host_setup_bounds_matches_oracle_bitwise(tiny):
         amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, d_lower=bad)
     assert e.value.status == 3
     s.close()
+
+
+def test_update_D_fine_is_galerkin_for_reused_interpolation(tiny):
+    # amgf_update_D_fine keeps P_l and brings every A_l to R_l A_new P_l (host setup only)
+    D2, _ = cg.draw_D_b(91, tiny.m, tiny.n, -2.0, 9.0)
+    s = amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True)
+    P_old = [s.export(1, l) for l in range(s.info.nlevels - 1)]
+    s.update_D(D2, keep_coarse=True)
+    o = oracle.Oracle(tiny.K, tiny.J, D2, build_amg=0)
+    A = o.S()
+    assert (s.export(0, 0) != A).nnz == 0
+    for l in range(s.info.nlevels - 1):
+        P = s.export(1, l)
+        assert (P != P_old[l]).nnz == 0
+        A = (P.T @ A @ P).tocsr()
+        Al = s.export(0, l + 1)
+        assert abs(Al - A).max() <= 1e-12 * abs(A).max()
+    s.close()

@@ -316,7 +316,7 @@ def run_gpu(args, rank, world, local):
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             tr = json.load(f)
         ent = tr.get(f"{args.config}:precision{args.precision}", {})
-        if ent.get("kernel_source_sha") == kernel_source_sha():
+        if ent.get("kernel_source_sha") == kernel_source_sha(args.precision):
             traffic = ent.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -385,15 +385,23 @@ def fp64_peak_tflops():
     return 152 * 2 * 2 * mhz * 1e6 / 1e12
 
 
-def kernel_source_sha():
-    """Hash of the source the roofline kernels are built from: the fine-level BSR3 kernels
-    (FP64 and mixed) and the host code that lays their operator out.  DRAM traffic stored in
-    profiles/roofline_traffic.json is used only while this hash is unchanged."""
+def kernel_source_sha(precision: int = 0):
+    """Hash of the source the roofline kernel of this precision is built from: the fine-level
+    FP64 BSR3 kernel (precision 0) or the mixed one (1-3), with the host code that lays its
+    operator out.  DRAM traffic stored in profiles/roofline_traffic.json is used only while
+    this hash is unchanged."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2505_18576_gb300", "csrc")
     k = open(os.path.join(csrc, "kernels.cuh")).read()
-    h.update(k[k.index("struct BsrArgs {"):k.index("// Coarsest-level solve out")].encode())
+    mid = k.index("// Fine level of the FP32 V-cycle")
+    if precision == 0:
+        h.update(k[k.index("struct BsrArgs {"):mid].encode())
+    else:
+        h.update(k[mid:k.index("// Coarsest-level solve out")].encode())
+        a = open(os.path.join(csrc, "amgf.cu")).read()
+        i = a.index("// fine-level K in 3x3 blocks")
+        h.update(a[i:a.index("// contact term J^T D J over all rows", i)].encode())
     c = open(os.path.join(csrc, "setup.cpp")).read()
     i = c.index("bool build_bsr3(")
     h.update(c[i:c.index("\nint validate_csr(", i)].encode())

@@ -44,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmds = [
             ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-I", INC,
              "-c", os.path.join(CSRC, "setup.cpp"), "-o", o_setup],
-            [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-I", INC, "-Xcompiler", "-fPIC",
+            [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-I", INC, "-Xcompiler", "-fPIC,-fopenmp",
              "-Xptxas", "-v" if verbose else "-O3",
              "-c", os.path.join(CSRC, "amgf.cu"), "-o", o_cuda],
         ]

@@ -327,7 +327,7 @@ static void launch_fine_mixed(Ctx& c, const float* x, const float* b, const floa
   if (c.k_bf16) {
     Bsr3MixedArgs<__nv_bfloat16> a{};
     fill(a);
-    a.v = (const __nv_bfloat16*)c.k_v;
+    a.pk = (const uint2*)c.k_v;
     if (result) bsr3_mixed_kernel<__nv_bfloat16, MODE, true><<<grid, TPB, 0, c.s>>>(a);
     else bsr3_mixed_kernel<__nv_bfloat16, MODE, false><<<grid, TPB, 0, c.s>>>(a);
   } else {
@@ -884,14 +884,35 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
     c.k_nslices = kb.nslices;
     c.k_nblocks = kb.nblocks;
     if ((st = c.upload(&c.k_soff, kb.soff.data(), kb.nslices + 1))) return st;
-    if ((st = c.upload(&c.k_bci, kb.bci.data(), (int64_t)kb.bci.size()))) return st;
     if (c.k_bf16) {
-      std::vector<__nv_bfloat16> v(kb.v.size());
-      for (size_t i = 0; i < v.size(); ++i) v[i] = __float2bfloat16_rn((float)kb.v[i]);
-      __nv_bfloat16* d = nullptr;
-      if ((st = c.upload(&d, v.data(), (int64_t)v.size()))) return st;
+      // packed: per block slot three 8-byte words {column, v0 v1}, {v2..v5}, {v6 v7 v8, 0},
+      // word p of slot (slice s, j, lane) at 3 soff[s] + (3 j + p) 32 + lane
+      std::vector<uint2> pk(3 * kb.bci.size());
+      auto bf = [](double x) -> uint32_t {
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+        uint16_t u;
+        memcpy(&u, &h, 2);
+        return u;
+      };
+#pragma omp parallel for schedule(static)
+      for (int64_t sl = 0; sl < kb.nslices; ++sl) {
+        const int64_t s0 = kb.soff[sl], w = (kb.soff[sl + 1] - s0) / BSR3::W;
+        for (int64_t j = 0; j < w; ++j)
+          for (int lane = 0; lane < BSR3::W; ++lane) {
+            const int64_t slot = s0 + BSR3::W * j + lane;
+            uint32_t q[9];
+            for (int t = 0; t < 9; ++t) q[t] = bf(kb.v[9 * s0 + (9 * j + t) * BSR3::W + lane]);
+            uint2* o = pk.data() + 3 * s0 + 3 * BSR3::W * j + lane;
+            o[0] = make_uint2((uint32_t)kb.bci[slot], q[0] | (q[1] << 16));
+            o[BSR3::W] = make_uint2(q[2] | (q[3] << 16), q[4] | (q[5] << 16));
+            o[2 * BSR3::W] = make_uint2(q[6] | (q[7] << 16), q[8]);
+          }
+      }
+      uint2* d = nullptr;
+      if ((st = c.upload(&d, pk.data(), (int64_t)pk.size()))) return st;
       c.k_v = d;
     } else {
+      if ((st = c.upload(&c.k_bci, kb.bci.data(), (int64_t)kb.bci.size()))) return st;
       std::vector<float> v(kb.v.begin(), kb.v.end());
       float* d = nullptr;
       if ((st = c.upload(&d, v.data(), (int64_t)v.size()))) return st;

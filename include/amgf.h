@@ -59,7 +59,7 @@ typedef struct {
   double strength_theta;  /* AMG strength threshold (0.55) */
   double rtol;            /* PCG stop: sqrt(r^T z / r0^T z0) < rtol (1e-8); Section 4 uses this norm */
   int max_levels;         /* AMG levels including the coarsest (25) */
-  int max_coarse;         /* stop coarsening at n_l <= max_coarse (128); coarsest solved exactly */
+  int max_coarse;         /* stop coarsening at n_l <= max_coarse (1200); coarsest solved exactly */
   int num_functions;      /* unknowns per node for the unknown approach (3); DOF i has function i % 3 */
   int nu;                 /* l1-Jacobi sweeps before and after the coarse correction (1) */
   int filter;             /* 1: AMGF (default); 0: plain AMG V-cycle, M = B */
@@ -83,6 +83,11 @@ typedef struct {
                              neighbours distributed over the strong C points, weak ones lumped;
                              rows whose lumped diagonal nearly vanishes use direct weights), the
                              default; 1 = direct interpolation with Stueben's sign split */
+  int p_max;              /* interpolation truncation (4; 0 = none): every F row of P_l with more
+                             weights keeps its p_max weights of largest magnitude (ties: smaller
+                             coarse index), scaled by (sum of all) / (sum of kept) so that the
+                             row sum is unchanged; rows whose kept weights sum to zero stay whole.
+                             Lowers the operator complexity of the coarse levels. */
 } amgf_options;
 
 typedef struct {

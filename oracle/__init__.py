@@ -45,7 +45,7 @@ class Opts(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("num_functions", ctypes.c_int),
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int),
                 ("contact_components", ctypes.c_int), ("build_amg", ctypes.c_int),
-                ("interp", ctypes.c_int)]
+                ("interp", ctypes.c_int), ("p_max", ctypes.c_int)]
 
 
 def _load():

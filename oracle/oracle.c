@@ -34,7 +34,10 @@
  *               magnitude takes direct interpolation with the sign split instead (positive
  *               entries lumped into the diagonal when no positive strong C neighbour).  Only
  *               same-function couplings enter.  interp = 1 selects direct interpolation
- *               everywhere.
+ *               everywhere.  p_max > 0 truncates every F row with more weights to its p_max
+ *               weights of largest magnitude (ties: smaller coarse index) and scales them by
+ *               (sum of all weights) / (sum of the kept ones), so the row sum (interpolation
+ *               of constants) is unchanged; a row whose kept weights sum to zero is left whole.
  *   Galerkin  : R = P^T, A_c = R (A P); every sum taken in ascending index order
  *   smoother  : nu sweeps of x <- x + (r - A x) / l1, l1_i = sum_j |a_ij|, zero start on the way
  *               down and the same sweeps on the way up (B symmetric)
@@ -68,7 +71,7 @@ typedef struct {
 
 typedef struct {
   double strength_theta; /* 0.8 */
-  int max_coarse;        /* 128 */
+  int max_coarse;        /* 1200 */
   int max_levels;        /* 25 */
   int num_functions;     /* 3: DOF i has function i % 3 on the finest level */
   int nu;                /* smoothing sweeps down and up (1) */
@@ -76,6 +79,7 @@ typedef struct {
   int contact_components;/* 0: I_c = nonzero columns of J; 1: all 3 DOFs of those nodes; 2: all DOFs */
   int build_amg;         /* 1: full setup; 0: assemble A only (for A x on large problems) */
   int interp;            /* 0: classical interpolation (default); 1: direct interpolation */
+  int p_max;             /* interpolation truncation: at most p_max weights per F row (4; 0: none) */
 } orc_opts;
 
 typedef struct {
@@ -368,6 +372,36 @@ static void direct_row(const ocsr* A, int64_t i, const int32_t* func, const int8
   }
 }
 
+/* Truncate the F row P->ci/P->v[row0 .. *nnz) (ascending coarse index) to its p_max weights of
+ * largest magnitude, ties to the smaller coarse index, rescaled to the old row sum; both
+ * sums run in ascending index order.  Selection by repeated maximum over the row. */
+static void truncate_row(ocsr* P, int64_t row0, int64_t* nnz, int p_max) {
+  const int64_t len = *nnz - row0;
+  if (p_max <= 0 || len <= p_max) return;
+  int8_t* keep = xcalloc(len, 1);
+  for (int t = 0; t < p_max; ++t) {
+    int64_t best = -1;
+    for (int64_t q = 0; q < len; ++q)
+      if (!keep[q] && (best < 0 || fabs(P->v[row0 + q]) > fabs(P->v[row0 + best]))) best = q;
+    keep[best] = 1;
+  }
+  double total = 0.0, kept = 0.0;
+  for (int64_t q = 0; q < len; ++q) total += P->v[row0 + q];
+  for (int64_t q = 0; q < len; ++q) if (keep[q]) kept += P->v[row0 + q];
+  if (kept != 0.0) {
+    const double scale = total / kept;
+    int64_t m = row0;
+    for (int64_t q = 0; q < len; ++q) {
+      if (!keep[q]) continue;
+      P->ci[m] = P->ci[row0 + q];
+      P->v[m] = P->v[row0 + q] * scale;
+      m++;
+    }
+    *nnz = m;
+  }
+  free(keep);
+}
+
 /* Interpolation P (n x n_c) from the C/F split.
  * interp = 0, classical interpolation (Ruge & Stueben), same-function couplings only:
  *   w_ij = -( a_ij + sum_{k in F_i^s} a_ik abar_kj / sum_{m in C_i^s} abar_km ) / d_i,
@@ -379,7 +413,7 @@ static void direct_row(const ocsr* A, int64_t i, const int32_t* func, const int8
  * C points interpolate by identity; F points without a strong C neighbour get an empty row. */
 #define CLASSICAL_GUARD 0.05
 static void build_interp(const ocsr* A, const ocsr* Sg, const int32_t* func, const int8_t* cf, int interp,
-                         ocsr* P, int64_t* ncoarse) {
+                         int p_max, ocsr* P, int64_t* ncoarse) {
   int64_t n = A->nrows;
   int64_t* cidx = xmalloc(n * sizeof(int64_t));
   int64_t nc = 0;
@@ -446,6 +480,7 @@ static void build_interp(const ocsr* A, const ocsr* Sg, const int32_t* func, con
       }
     }
     for (int64_t k = Sg->rp[i]; k < Sg->rp[i + 1]; ++k) strong[Sg->ci[k]] = 0;
+    truncate_row(P, P->rp[i], &nnz, p_max);
     P->rp[i + 1] = nnz;
   }
   free(strong); free(pos); free(cidx);
@@ -512,7 +547,7 @@ static int amg_setup(orc_t* h) {
     g->cf[l] = xmalloc(n);
     rs_coarsen(&Sg, g->cf[l]);
     int64_t nc = 0;
-    build_interp(A, &Sg, g->func[l], g->cf[l], o->interp, &g->P[l], &nc);
+    build_interp(A, &Sg, g->func[l], g->cf[l], o->interp, o->p_max, &g->P[l], &nc);
     csr_free(&Sg);
     if (nc == 0 || nc == n) { /* coarsening stalled: this level is the coarsest */
       csr_free(&g->P[l]); free(g->cf[l]); g->cf[l] = NULL;
@@ -726,7 +761,7 @@ static void filter_solve(orc_t* h, const double* v, double* w) {
 
 void orc_opts_default(orc_opts* o) {
   o->strength_theta = 0.55;
-  o->max_coarse = 128;
+  o->max_coarse = 1200;
   o->max_levels = 25;
   o->num_functions = 3;
   o->nu = 1;
@@ -734,6 +769,7 @@ void orc_opts_default(orc_opts* o) {
   o->contact_components = 0;
   o->build_amg = 1;
   o->interp = 0;
+  o->p_max = 4;
 }
 
 const char* orc_error(orc_t* h) { return h ? h->err : "null handle"; }

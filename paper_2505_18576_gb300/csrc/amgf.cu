@@ -339,6 +339,13 @@ static void launch_fine_mixed(Ctx& c, const float* x, const float* b, const floa
   }
 }
 
+// coarsest-level solve: one warp per row of the dense inverse
+static int dense_grid(const Ctx& c) {
+  const int64_t g = (c.nL + DENSE_ROWS_TPB / 32 - 1) / (DENSE_ROWS_TPB / 32);
+  const int64_t cap = (int64_t)c.num_sms * 8;
+  return (int)(g < 1 ? 1 : (g < cap ? g : cap));
+}
+
 static int vec_grid(const Ctx& c, int64_t n) {
   int64_t g = (n + TPB - 1) / TPB;
   const int64_t cap = (int64_t)c.num_sms * 8;
@@ -382,8 +389,10 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
     const int lc = nlev - 1;
     const double* rc = rhs_of(lc);
     double* oc = lc == 0 ? out0 : c.L[lc].out;
-    dense_gemv_kernel<<<1, DENSE_TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, lc == 0 ? add0 : nullptr, oc,
-                                          lc == 0 ? dotv : nullptr, lc == 0 ? dotres : nullptr);
+    if (lc == 0)
+      dense_gemv_kernel<<<1, DENSE_TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, add0, oc, dotv, dotres);
+    else
+      dense_rows_kernel<double><<<dense_grid(c), DENSE_ROWS_TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, oc);
     c.launches++;
   }
   for (int l = nlev - 2; l >= 0; --l) {
@@ -438,7 +447,8 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
       launch_csr_f<M_SPMV>(c, lv.Rf, rs);
     }
   }
-  dense_gemv_f32_kernel<<<1, DENSE_TPB, 0, c.s>>>(c.nL, c.coarse_inv_f, c.L[nlev - 1].rhsf, c.L[nlev - 1].outf);
+  dense_rows_kernel<float><<<dense_grid(c), DENSE_ROWS_TPB, 0, c.s>>>(c.nL, c.coarse_inv_f, c.L[nlev - 1].rhsf,
+                                                                       c.L[nlev - 1].outf);
   c.launches++;
   for (int l = nlev - 2; l >= 0; --l) {
     DLevel& lv = c.L[l];
@@ -1070,7 +1080,7 @@ int amgf_options_default(amgf_options* o) {
   o->strength_theta = 0.55;
   o->rtol = 1e-8;
   o->max_levels = 25;
-  o->max_coarse = 128;
+  o->max_coarse = 1200;
   o->num_functions = 3;
   o->nu = 1;
   o->filter = 1;
@@ -1081,6 +1091,7 @@ int amgf_options_default(amgf_options* o) {
   o->precision = 0;
   o->filter_algo = 0;
   o->interp = 0;
+  o->p_max = 4;
   return AMGF_OK;
 }
 
@@ -1106,7 +1117,7 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
   if (opt.nu < 1 || opt.max_levels < 1 || opt.max_coarse < 1 || opt.num_functions < 1 || !(opt.rtol > 0.0) ||
       opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2 || opt.precision < 0 ||
       opt.precision > 3 || opt.filter_algo < 0 || opt.filter_algo > 1 ||
-      opt.interp < 0 || opt.interp > 1)
+      opt.interp < 0 || opt.interp > 1 || opt.p_max < 0)
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");

@@ -11,7 +11,7 @@
 //       POST      y = x + W (b - A x) [+ add]      (l1-Jacobi sweep; z = y2 + B r2)
 //     with W = diag(1 / l1), and optionally a deterministic dot product of the output
 //     with another vector (p^T A p, r^T z) finished by the last block to arrive.
-//   - dense_gemv: coarsest-level solve with the host-computed inverse.
+//   - dense_gemv / dense_rows: coarsest-level solve with the host-computed inverse.
 //   - filter_bcr: one phase of the odd-even block cyclic reduction solve of the
 //     block-tridiagonal A_w (Section 5.1 filter step): all block GEMVs of a reduction
 //     level at once over the whole GPU.
@@ -345,24 +345,11 @@ __global__ void __launch_bounds__(TPB) bsr3_mixed_kernel(Bsr3MixedArgs<VT> a) {
   if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
 }
 
-// out = Ainv * r, single precision, one block (coarsest level of the FP32 V-cycle)
-// Coarsest-level solve out = A_L^{-1} r with the host-computed dense inverse: one CTA of
-// DENSE_TPB threads, a warp per row (the rows' loads are independent, so 32 warps keep
-// enough of them in flight; the solve is latency bound at n_L <= 128).
+// Coarsest-level solve out = A_L^{-1} r with the host-computed dense inverse. A V-cycle
+// with a single level needs the add and dot outputs: one CTA of DENSE_TPB threads, a warp
+// per row (dense_gemv_kernel). Every other coarsest solve spreads its rows over the grid
+// (dense_rows_kernel, FP64 or FP32).
 constexpr int DENSE_TPB = 1024;
-
-__global__ void __launch_bounds__(DENSE_TPB) dense_gemv_f32_kernel(int64_t n, const float* __restrict__ Ainv,
-                                                             const float* __restrict__ r, float* out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int64_t i = warp; i < n; i += nw) {
-    const float* row = Ainv + i * n;
-    float s = 0.f;
-    for (int64_t k = lane; k < n; k += 32) s += row[k] * r[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) out[i] = s;
-  }
-}
 
 // x_i += W_i * res_i in FP32 (extra sweeps when nu > 1)
 __global__ void axpy_w_f32_kernel(int64_t n, const float* __restrict__ winv, const float* __restrict__ res, float* x) {
@@ -389,6 +376,27 @@ __global__ void scale_kernel(int64_t n, const double* __restrict__ w, const doub
 __global__ void axpy_w_kernel(int64_t n, const double* __restrict__ winv, const double* __restrict__ res, double* x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] += winv[i] * res[i];
+}
+
+// out = Ainv * r with the rows spread over the grid: a warp per row, grid-stride, the
+// row's loads coalesced across the warp and summed by the same lane split and butterfly as
+// dense_gemv_kernel (so both give the same bits). For coarsest levels of a few thousand
+// rows, whose inverse (n^2 values) is too large for one CTA to stream quickly.
+constexpr int DENSE_ROWS_TPB = 256;
+template <typename T>
+__global__ void __launch_bounds__(DENSE_ROWS_TPB) dense_rows_kernel(int64_t n, const T* __restrict__ Ainv,
+                                                                    const T* __restrict__ r, T* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * DENSE_ROWS_TPB + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * DENSE_ROWS_TPB) >> 5;
+  for (int64_t i = w0; i < n; i += nw) {
+    const T* row = Ainv + i * n;
+    T s = 0;
+    for (int64_t k = lane; k < n; k += 32) s += row[k] * r[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[i] = s;
+  }
 }
 
 // out = Ainv * r (+ add), Ainv dense n x n row-major; optional dot(dotv, out). One block.

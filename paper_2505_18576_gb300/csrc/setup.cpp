@@ -227,7 +227,8 @@ std::vector<int8_t> ruge_stueben(int64_t n, const std::vector<int64_t>& srp, con
 constexpr double kClassicalGuard = 0.05;
 
 HCSR build_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const std::vector<int32_t>& sci,
-                         const std::vector<int32_t>& func, const std::vector<int8_t>& cf, int interp, int64_t& nc) {
+                         const std::vector<int32_t>& func, const std::vector<int8_t>& cf, int interp, int p_max,
+                         int64_t& nc) {
   const int64_t n = A.nrows;
   std::vector<int64_t> cidx(n, -1);
   nc = 0;
@@ -243,6 +244,37 @@ HCSR build_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const s
     auto& V = pc.v[t];
     std::vector<int32_t> ccol;  // strong C neighbours of the row (ascending) and their accumulators
     std::vector<double> cval;
+    std::vector<int32_t> order;
+    std::vector<int8_t> kept;
+    // P_max truncation of the row just appended (weights in ascending coarse index): keep the
+    // p_max largest |w| (ties: smaller coarse index), scaled by sum(all) / sum(kept)
+    auto truncate_last = [&]() {
+      const int64_t cnt = L.back();
+      if (p_max <= 0 || cnt <= p_max) return;
+      const size_t r0 = V.size() - (size_t)cnt;
+      order.resize(cnt);
+      for (int64_t q = 0; q < cnt; ++q) order[q] = (int32_t)q;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int32_t x, int32_t y) { return std::fabs(V[r0 + x]) > std::fabs(V[r0 + y]); });
+      kept.assign(cnt, 0);
+      for (int q = 0; q < p_max; ++q) kept[order[q]] = 1;
+      double all = 0.0, part = 0.0;
+      for (int64_t q = 0; q < cnt; ++q) all += V[r0 + q];
+      for (int64_t q = 0; q < cnt; ++q)
+        if (kept[q]) part += V[r0 + q];
+      if (part == 0.0) return;
+      const double scale = all / part;
+      size_t m = r0;
+      for (int64_t q = 0; q < cnt; ++q) {
+        if (!kept[q]) continue;
+        C[m] = C[r0 + q];
+        V[m] = V[r0 + q] * scale;
+        ++m;
+      }
+      C.resize(m);
+      V.resize(m);
+      L.back() = p_max;
+    };
     // direct interpolation weights of F row i (walks row i of A and the ascending strong list together)
     auto direct_row = [&](int64_t i) {
       double diag = 0.0, sn = 0.0, sp = 0.0, cn = 0.0, cp = 0.0;
@@ -280,7 +312,7 @@ HCSR build_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const s
       bool anyC = false;
       for (int64_t k = srp[i]; k < srp[i + 1]; ++k) anyC |= cf[sci[k]] != 0;
       if (!anyC) { L.push_back(0); continue; }
-      if (interp == 1) { direct_row(i); continue; }
+      if (interp == 1) { direct_row(i); truncate_last(); continue; }
       // classical: numerators start at a_ij for the strong C neighbours
       ccol.clear();
       cval.clear();
@@ -328,12 +360,13 @@ HCSR build_interpolation(const HCSR& A, const std::vector<int64_t>& srp, const s
           if ((am < 0.0) != (ajj < 0.0)) cval[c] += a * am / den;
         }
       }
-      if (std::fabs(diag) < kClassicalGuard * aii) { direct_row(i); continue; }
+      if (std::fabs(diag) < kClassicalGuard * aii) { direct_row(i); truncate_last(); continue; }
       for (size_t c = 0; c < ccol.size(); ++c) {
         C.push_back((int32_t)cidx[ccol[c]]);
         V.push_back(-cval[c] / diag);
       }
       L.push_back((int64_t)ccol.size());
+      truncate_last();
     }
   }
   HCSR P;
@@ -760,7 +793,7 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
     std::vector<int8_t> cf = ruge_stueben(n, srp, sci);
     double t2 = now();
     int64_t nc = 0;
-    HCSR P = build_interpolation(A, srp, sci, H.func[l], cf, o.interp, nc);
+    HCSR P = build_interpolation(A, srp, sci, H.func[l], cf, o.interp, o.p_max, nc);
     double t3 = now();
     t_str += t1 - t0; t_rs += t2 - t1; t_int += t3 - t2;
     if (nc == 0 || nc == n) break;  // coarsening stalled: this level is the coarsest

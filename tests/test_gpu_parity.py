@@ -58,13 +58,18 @@ CASES = {
     "tiny": dict(nx=8, ny=8, nz=4, d_lo=-2, d_hi=4),
     "ragged": dict(nx=5, ny=3, nz=2, d_lo=-2, d_hi=8),
     "n16": dict(nx=16, ny=12, nz=7, d_lo=-2, d_hi=8),
+    "n16_deep": dict(nx=16, ny=12, nz=7, d_lo=-2, d_hi=8),
 }
+# the default hierarchy (coarsest <= 1200 rows, 4 weights per interpolation row) has two to
+# four levels on these sizes; n16_deep keeps coarsening to 128 rows without truncation, so
+# that every level kind (long coarse rows, a warp per row, tiny levels) runs
+OPTS = {"n16_deep": dict(max_coarse=128, p_max=0)}
 
 
 @pytest.fixture(scope="module", params=list(CASES))
 def case(request):
     p = cg.make_problem(None, seed=1, **CASES[request.param])
-    o, s = _pair(p)
+    o, s = _pair(p, **OPTS.get(request.param, {}))
     yield request.param, p, o, s
     s.close()
 
@@ -124,7 +129,7 @@ def test_filter_sweep_algorithm_parity(case):
     import paper_2505_18576_gb300 as m
     name, p, o, _ = case
     kap, Aw = kappa_Aw(o)
-    s1 = m.Solver(p.K, p.J, p.D, filter_algo=1)
+    s1 = m.Solver(p.K, p.J, p.D, filter_algo=1, **OPTS.get(name, {}))
     try:
         rng = np.random.default_rng(2)
         v = rng.standard_normal(o.nc)
@@ -195,7 +200,7 @@ def test_pcg_tight_solution_match(case):
     import paper_2505_18576_gb300 as m
     name, p, o, s = case
     xo, ko, sto, al, be, _ = o.pcg(p.b, tol=1e-12)
-    st_ = m.Solver(p.K, p.J, p.D, rtol=1e-12)
+    st_ = m.Solver(p.K, p.J, p.D, rtol=1e-12, **OPTS.get(name, {}))
     x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
     st = st_.pcg_solve(dev(p.b), x)
     assert sto == 0 and st.status == 0
@@ -214,7 +219,7 @@ def test_pcg_deterministic_and_graph_equals_stream(case):
     s1 = s.pcg_solve(dev(p.b), x1)
     s2 = s.pcg_solve(dev(p.b), x2)
     assert s1.iters == s2.iters and torch.equal(x1, x2)
-    s_ng = m.Solver(p.K, p.J, p.D, use_graph=0)
+    s_ng = m.Solver(p.K, p.J, p.D, use_graph=0, **OPTS.get(name, {}))
     x3 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
     s3 = s_ng.pcg_solve(dev(p.b), x3)
     assert s3.iters == s1.iters and torch.equal(x1, x3)

@@ -62,6 +62,15 @@ def test_host_setup_matches_oracle_options(tiny):
     _compare_hierarchy(tiny, interp=1, strength_theta=0.8)
     _compare_hierarchy(tiny, contact_components=1)
     _compare_hierarchy(tiny, max_coarse=400)
+    _compare_hierarchy(tiny, p_max=4)
+    _compare_hierarchy(tiny, p_max=2, interp=1)
+
+
+def test_host_setup_truncated_matches_oracle_bitwise():
+    # rows of the coarser levels carry many more weights than 4, so the truncation acts
+    p = cg.make_problem(None, nx=16, ny=16, nz=8, d_lo=-2, d_hi=8, seed=3)
+    _compare_hierarchy(p, p_max=4)
+    _compare_hierarchy(p, p_max=3)
 
 
 def test_host_setup_no_contact(tiny):
@@ -111,7 +120,7 @@ def test_invalid_inputs(tiny):
     with pytest.raises(amgf.AmgfError) as e:
         amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, precision=4)
     assert e.value.status == 1
-    for bad_opt in (dict(filter_algo=2), dict(interp=2)):
+    for bad_opt in (dict(filter_algo=2), dict(interp=2), dict(p_max=-1)):
         with pytest.raises(amgf.AmgfError) as e:
             amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, **bad_opt)
         assert e.value.status == 1

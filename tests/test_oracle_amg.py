@@ -86,6 +86,30 @@ def test_classical_interpolation_hand_derived():
     Pd = od.P(0).toarray()
     for row, w in g["P_rows_direct"].items():
         assert np.allclose(Pd[int(row)], w, rtol=0, atol=1e-15)
+    # truncation to one weight per row, rescaled to the row sum (hand-derived in the golden file)
+    ot = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=2, filter=0, strength_theta=0.5, p_max=1)
+    Pt = ot.P(0).toarray()
+    for row, w in g["P_rows_pmax1"].items():
+        assert np.allclose(Pt[int(row)], w, rtol=0, atol=1e-15)
+    assert np.array_equal(np.diff(ot.P(0).indptr), np.ones(6, dtype=np.int64))
+
+
+def test_truncation_1d_laplacian_ties():
+    # 1D Laplacian: every interior F point interpolates 1/2, 1/2 from its two C neighbours.
+    # p_max = 1 keeps the tie's smaller coarse index and rescales it to the row sum 1; the
+    # boundary F points have one weight (1/2) and stay as they are.
+    n = 33
+    k = (n - 1) // 2
+    o = oracle.Oracle(csr_of(lap1d(n)), num_functions=1, max_coarse=4, filter=0, strength_theta=0.25, p_max=1)
+    P = o.P(0).toarray()
+    Pref = np.zeros((n, k))
+    for c in range(k):
+        Pref[2 * c + 1, c] = 1.0
+    Pref[0, 0] = 0.5
+    Pref[n - 1, k - 1] = 0.5
+    for c in range(1, k):
+        Pref[2 * c, c - 1] = 1.0
+    assert np.array_equal(P, Pref)
 
 
 def test_classical_guard_falls_back_to_direct():
@@ -127,24 +151,32 @@ def _zero_rowsum_matrix(n, seed):
     return (A + sp.diags(d)).tocsr()
 
 
+@pytest.mark.parametrize("p_max", [0, 2])
 @pytest.mark.parametrize("interp", [0, 1])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_interpolation_preserves_constants(seed, interp):
+def test_interpolation_preserves_constants(seed, interp, p_max):
     # For zero row sums, both classical interpolation (distributed strong F couplings, lumped
     # weak ones) and direct interpolation with the sign split reproduce constants exactly on
-    # every F row that has a strong C neighbour (Ruge & Stueben's and Stueben's constructions).
+    # every F row that has a strong C neighbour (Ruge & Stueben's and Stueben's constructions);
+    # truncation rescales the kept weights to the row sum, so it keeps that property.
     A = _zero_rowsum_matrix(400, seed)
     A = A + sp.identity(400) * 1e-12 * abs(A).max()
-    o = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=20, filter=0, strength_theta=0.25, interp=interp)
+    o = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=20, filter=0, strength_theta=0.25, interp=interp,
+                      p_max=p_max)
     P = o.P(0)
     s = P @ np.ones(P.shape[1])
     has = np.diff(P.indptr) > 0
     assert has.sum() > 300
     assert np.allclose(s[has], 1.0, rtol=0, atol=1e-8)
+    if p_max:
+        assert np.diff(P.indptr).max() <= p_max
+        full = oracle.Oracle(csr_of(A), num_functions=1, max_coarse=20, filter=0, strength_theta=0.25,
+                             interp=interp).P(0)
+        assert np.diff(full.indptr).max() > p_max  # the truncation had rows to act on
 
 
 def test_galerkin_product_and_transpose(tiny):
-    o = oracle.Oracle(tiny.K, tiny.J, tiny.D)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, max_coarse=128)
     assert o.nlev >= 3
     for l in range(o.nlev - 1):
         A, P, R, Ac = o.A(l), o.P(l), o.R(l), o.A(l + 1)
@@ -162,7 +194,7 @@ def test_galerkin_product_and_transpose(tiny):
 
 def test_strength_is_componentwise(tiny):
     # interpolation only couples DOFs of the same displacement component
-    o = oracle.Oracle(tiny.K, tiny.J, tiny.D)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, max_coarse=128)
     for l in range(o.nlev - 1):
         P = o.P(l).tocoo()
         fc, ff = o.func(l + 1), o.func(l)
@@ -184,7 +216,7 @@ def _dense_B(o, l):
 
 
 def test_vcycle_error_propagation_identity(tiny):
-    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, filter=0)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, filter=0, max_coarse=128)
     n = tiny.n
     Bref = _dense_B(o, 0)
     rng = np.random.default_rng(3)
@@ -196,7 +228,7 @@ def test_vcycle_error_propagation_identity(tiny):
 
 
 def test_vcycle_symmetric_convergent(tiny):
-    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, filter=0)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, filter=0, max_coarse=128)
     n = tiny.n
     B = np.column_stack([o.vcycle(e) for e in np.eye(n)])
     assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
@@ -208,14 +240,14 @@ def test_vcycle_symmetric_convergent(tiny):
 
 
 def test_l1_row_sums(tiny):
-    o = oracle.Oracle(tiny.K, tiny.J, tiny.D)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, max_coarse=128)
     for l in range(o.nlev):
         A = o.A(l)
         assert np.allclose(o.l1(l), np.asarray(abs(A).sum(axis=1)).ravel(), rtol=1e-14)
 
 
 def test_assembled_schur_complement(tiny):
-    o = oracle.Oracle(tiny.K, tiny.J, tiny.D)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, max_coarse=128)
     K, J = tiny.K.to_scipy(), tiny.J.to_scipy()
     ref = (K + J.T @ sp.diags(tiny.D) @ J).toarray()
     assert np.abs(o.S().toarray() - ref).max() <= 1e-15 * np.abs(ref).max()

@@ -88,6 +88,9 @@ typedef struct {
                              coarse index), scaled by (sum of all) / (sum of kept) so that the
                              row sum is unchanged; rows whose kept weights sum to zero stay whole.
                              Lowers the operator complexity of the coarse levels. */
+  int update_in_place;    /* 1 (default): amgf_update_D_fine writes the new values into the
+                             device image (same arrays, same solve graph); 0: it rebuilds and
+                             uploads the whole image, as amgf_update_D does */
 } amgf_options;
 
 typedef struct {
@@ -149,8 +152,14 @@ int amgf_update_D(amgf_handle h, const double* D);
  * the old P_l.  B therefore stays the V-cycle of a Galerkin hierarchy of the current A (and
  * M stays SPD, lambda_max(B A) <= 1); only its interpolation is from an earlier A, so PCG may
  * need more iterations.  Skips strength, coarsening, interpolation and the full Galerkin
- * products (most of the setup time).  Falls back to amgf_update_D when the hierarchy has one
- * level or an update would leave a coarse pattern.  Errors as amgf_update_D. */
+ * products (most of the setup time).  With options.update_in_place (default) only values move
+ * on the device: the contact rows of A (their 32-row slices of the fine-level image), the
+ * touched coarse entries, l1 weights, the coarsest inverse, the filter matrices and the
+ * learned smoother's inputs, written into the existing arrays (the solve graph stays valid);
+ * the results equal those of a full re-upload bit for bit.  Falls back to the full re-upload
+ * when a bound diagonal is present or the filter's layout changes, and to amgf_update_D when
+ * the hierarchy has one level or an update would leave a coarse pattern.  Errors as
+ * amgf_update_D. */
 int amgf_update_D_fine(amgf_handle h, const double* D);
 
 /* Bound-constrained variant (Section 3, remark on bound constraints): with the additional

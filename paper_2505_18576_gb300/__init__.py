@@ -52,7 +52,7 @@ class Options(ctypes.Structure):
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int), ("contact_components", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("precision", ctypes.c_int), ("filter_algo", ctypes.c_int),
-                ("interp", ctypes.c_int), ("p_max", ctypes.c_int)]
+                ("interp", ctypes.c_int), ("p_max", ctypes.c_int), ("update_in_place", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

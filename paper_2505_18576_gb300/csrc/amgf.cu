@@ -18,6 +18,7 @@
 // host round trip until it ends.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -94,6 +95,9 @@ struct Ctx {
   HCSR Kh, Jh;
   std::vector<double> Eh;  // bound-constraint diagonal D_lo + D_hi (empty: none)
   std::vector<double> Dh;  // D of the current A (for amgf_update_D_fine)
+  BSR3 bsr0;               // layout (soff, bci) of the fine-level BSR3 on the device, values dropped
+  int64_t fM_count = 0;    // doubles in fM
+  int64_t c_nnz = 0;       // entries of the contact-term CSR (mixed precision)
   Hierarchy H;
   Filter F;
   amgf_info info{};
@@ -771,6 +775,182 @@ static void fill_info(Ctx& c) {
   in.filter_nblocks = c.F.nblk;
 }
 
+// dst[idx[k]] = val[k] on the device (temporary buffers, synchronous)
+template <typename T>
+static int scatter_to_device(Ctx& c, T* dst, const std::vector<int64_t>& idx, const std::vector<T>& val) {
+  if (idx.empty()) return AMGF_OK;
+  const int64_t n = (int64_t)idx.size();
+  int64_t* di = nullptr;
+  T* dv = nullptr;
+  if (cudaMalloc(&di, n * sizeof(int64_t)) != cudaSuccess) return fail(AMGF_ERR_OOM, "cudaMalloc (update)");
+  if (cudaMalloc(&dv, n * sizeof(T)) != cudaSuccess) { cudaFree(di); return fail(AMGF_ERR_OOM, "cudaMalloc (update)"); }
+  // the copies from pageable memory complete asynchronously: synchronise before the kernel
+  cudaError_t e = cudaMemcpy(di, idx.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dv, val.data(), n * sizeof(T), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) {
+    scatter_kernel<T><<<vec_grid(c, n), TPB, 0, c.s>>>(n, di, dv, dst);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s);
+  }
+  cudaFree(di);
+  cudaFree(dv);
+  if (e != cudaSuccess) return fail(AMGF_ERR_CUDA, std::string("update scatter: ") + cudaGetErrorString(e));
+  return AMGF_OK;
+}
+
+template <typename T>
+static int copy_to_device(T* dst, const T* src, int64_t n) {
+  if (n <= 0) return AMGF_OK;
+  CK(cudaMemcpy(dst, src, (size_t)n * sizeof(T), cudaMemcpyHostToDevice));
+  return AMGF_OK;
+}
+
+// amgf_update_D_fine in place: only D changed, the interpolation is reused, so every device
+// array keeps its size and pattern and only values move: the contact rows of A_0 (their
+// 32-row slices of the BSR3 image), the Galerkin-updated entries of the coarse A_l, the l1
+// weights, the coarsest inverse, the mixed path's FP64 contact term, the filter matrices and
+// the learned smoother's inputs.  Host arithmetic is that of the full update.  The solve graph
+// stays valid (no pointer changes).  Returns kFallback when the new operator does not fit the
+// device image (the caller then takes the full path; the hierarchy is consistent with D), and
+// kRebuild when a coarse update left the coarse patterns (a new hierarchy is needed).
+static constexpr int kFallback = -100, kRebuild = -101;
+static int update_D_in_place(Ctx& c, const double* D, const amgf_csr& K, const amgf_csr& J, std::string& err) {
+  auto t_start = std::chrono::steady_clock::now();
+  auto since = [](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
+  };
+  const int nlev = c.H.nlev();
+  if (c.host_only || nlev < 2 || (int)c.L.size() != nlev || !c.Eh.empty() || c.m == 0 ||
+      (int64_t)c.Dh.size() != c.m || c.H.A[0].nrows != c.n)
+    return kFallback;
+  DLevel& l0 = c.L[0];
+  if (l0.A.bsr && c.bsr0.soff.empty()) return kFallback;
+  if (c.o.filter && c.F.nc > 0 && c.F.algo == 0 && c.fM_count == 0) return kFallback;
+  // host: contact rows of A_0 as a fresh assembly writes them
+  std::vector<int64_t> rows;
+  int st = refresh_contact_rows(c.H.A[0], &K, &J, D, rows, err);
+  if (st == AMGF_ERR_INVALID_ARG) return kFallback;
+  if (st) return st;
+  const double t_assemble = since(t_start);
+  auto t1 = std::chrono::steady_clock::now();
+  // coarse levels: Galerkin products of the contact change, l1 sums, coarsest inverse
+  std::vector<double> dD(c.m);
+  for (int64_t r = 0; r < c.m; ++r) dD[r] = D[r] - c.Dh[r];
+  std::vector<std::vector<int64_t>> changed;
+  st = update_hierarchy_contact(c.H, nullptr, &J, dD.data(), &changed, err);
+  if (st == AMGF_ERR_INVALID_ARG) return kRebuild;
+  if (st) return st;
+  c.Dh.assign(D, D + c.m);
+  const double t_hier = since(t1);
+  t1 = std::chrono::steady_clock::now();
+  Filter F2;
+  const bool filt = c.o.filter && c.F.nc > 0;
+  if (filt) {
+    if ((st = build_filter(c.H.A[0], &J, c.o, F2, err))) return st;
+    const bool same = F2.nc == c.F.nc && F2.nb == c.F.nb && F2.nblk == c.F.nblk && F2.algo == c.F.algo &&
+                      F2.gidx == c.F.gidx && F2.touch_rows == c.F.touch_rows &&
+                      F2.tasks.size() == c.F.tasks.size() &&
+                      (F2.tasks.empty() ||
+                       std::memcmp(F2.tasks.data(), c.F.tasks.data(), F2.tasks.size() * sizeof(FilterTask)) == 0) &&
+                      F2.Sc.nnz() == c.fSc.nnz && (F2.algo != 0 || (int64_t)F2.M.size() == c.fM_count);
+    if (!same) return kFallback;
+  }
+  const double t_filter = since(t1);
+  std::vector<std::vector<float>> feat;
+  smoother_features(c.H, &J, D, nullptr, c.n, feat);
+  // ---- device, in place (nothing of an earlier call may still read these arrays; copies
+  // from pageable memory may still be in flight when cudaMemcpy returns, so the device is
+  // synchronised again at the end)
+  CK(cudaDeviceSynchronize());
+  if (l0.A.bsr) {
+    std::vector<int64_t> sl;
+    sl.reserve(rows.size());
+    for (int64_t a : rows) sl.push_back(a / 3 / BSR3::W);
+    std::sort(sl.begin(), sl.end());
+    sl.erase(std::unique(sl.begin(), sl.end()), sl.end());
+    std::vector<double> buf;
+    for (int64_t q : sl) {
+      const int64_t s0 = c.bsr0.soff[q], len = 9 * (c.bsr0.soff[q + 1] - s0);
+      buf.resize(len);
+      bsr3_fill_slice(c.H.A[0], c.bsr0, q, buf.data());
+      if ((st = copy_to_device(l0.A.bv + 9 * s0, buf.data(), len))) return st;
+    }
+  } else {
+    std::vector<int64_t> idx;
+    std::vector<double> val;
+    for (int64_t a : rows)
+      for (int64_t k = c.H.A[0].rp[a]; k < c.H.A[0].rp[a + 1]; ++k) { idx.push_back(k); val.push_back(c.H.A[0].v[k]); }
+    if ((st = scatter_to_device(c, l0.A.v, idx, val))) return st;
+  }
+  for (int l = 1; l < nlev; ++l) {
+    const std::vector<int64_t>& idx = changed[l];
+    if (idx.empty()) continue;
+    const HCSR& A = c.H.A[l];
+    DLevel& lv = c.L[l];
+    if (!c.mixed) {
+      std::vector<double> val(idx.size());
+      for (size_t k = 0; k < idx.size(); ++k) val[k] = A.v[idx[k]];
+      if ((st = scatter_to_device(c, lv.A.v, idx, val))) return st;
+    } else if (lv.Af.vb) {
+      std::vector<__nv_bfloat16> val(idx.size());
+      for (size_t k = 0; k < idx.size(); ++k) val[k] = __float2bfloat16_rn((float)A.v[idx[k]]);
+      if ((st = scatter_to_device(c, lv.Af.vb, idx, val))) return st;
+    } else {
+      std::vector<float> val(idx.size());
+      for (size_t k = 0; k < idx.size(); ++k) val[k] = (float)A.v[idx[k]];
+      if ((st = scatter_to_device(c, lv.Af.v, idx, val))) return st;
+    }
+  }
+  for (int l = 0; l < nlev; ++l) {
+    DLevel& lv = c.L[l];
+    std::vector<double> w(lv.n);
+    for (int64_t i = 0; i < lv.n; ++i) w[i] = 1.0 / c.H.l1[l][i];
+    if (lv.winv && (st = copy_to_device(lv.winv, w.data(), lv.n))) return st;
+    if (lv.winvf) {
+      std::vector<float> wf(w.begin(), w.end());
+      if ((st = copy_to_device(lv.winvf, wf.data(), lv.n))) return st;
+    }
+    if (l + 1 < nlev) {
+      if ((st = copy_to_device(c.feat_d[l], feat[l].data(), (int64_t)feat[l].size()))) return st;
+      if ((st = copy_to_device(c.l1_d[l], c.H.l1[l].data(), lv.n))) return st;
+    }
+  }
+  if (c.H.n_coarse != c.nL) return kRebuild;
+  if (!c.mixed) {
+    if ((st = copy_to_device(c.coarse_inv, c.H.coarse_inv.data(), c.nL * c.nL))) return st;
+  } else {
+    std::vector<float> ci(c.H.coarse_inv.begin(), c.H.coarse_inv.end());
+    if ((st = copy_to_device(c.coarse_inv_f, ci.data(), c.nL * c.nL))) return st;
+    std::vector<int64_t> zrp(c.n + 1, 0);
+    amgf_csr Z{c.n, c.n, 0, zrp.data(), nullptr, nullptr};
+    HCSR C;
+    if ((st = assemble_S(&Z, &J, D, C, err))) return st;
+    if (C.nnz() != c.c_nnz) return kRebuild;
+    if ((st = copy_to_device(c.c_v, C.v.data(), C.nnz()))) return st;
+  }
+  if (filt) {
+    const int64_t tot = F2.nb * F2.nblk;
+    if (F2.algo == 0) {
+      if ((st = copy_to_device(c.fM, F2.M.data(), (int64_t)F2.M.size()))) return st;
+      std::vector<double>().swap(F2.M);
+    } else {
+      if ((st = copy_to_device(c.fG, F2.G.data(), tot * F2.nb))) return st;
+      if ((st = copy_to_device(c.fGT, F2.GT.data(), tot * F2.nb))) return st;
+      if ((st = copy_to_device(c.fDinv, F2.Dinv.data(), tot * F2.nb))) return st;
+    }
+    if ((st = copy_to_device(c.fSc.v, F2.Sc.v.data(), F2.Sc.nnz()))) return st;
+    c.F = std::move(F2);
+  }
+  CK(cudaDeviceSynchronize());
+  fill_info(c);
+  c.info.t_assemble_s = t_assemble;
+  c.info.t_hierarchy_s = t_hier;
+  c.info.t_filter_s = t_filter;
+  c.info.t_setup_s = since(t_start);
+  return AMGF_OK;
+}
+
 // keep_coarse: new fine-level operator (and filter) for D, coarse levels of B kept from the
 // last full setup (amgf_update_D_fine)
 static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
@@ -781,6 +961,13 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   auto since = [](std::chrono::steady_clock::time_point t) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t).count();
   };
+  if (keep_coarse && !c.host_only && c.o.update_in_place) {
+    const int r = update_D_in_place(c, D, K, J, err);
+    if (r == AMGF_OK) return AMGF_OK;
+    if (r == kRebuild) keep_coarse = false;
+    else if (r != kFallback) return fail(r, err);
+    err.clear();
+  }
   HCSR S;
   int st = assemble_S(&K, c.m > 0 ? &J : nullptr, D, S, err);
   if (st) return fail(st, err);
@@ -792,7 +979,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   if (keep_coarse && c.H.nlev() >= 2 && c.H.A[0].nrows == S.nrows && (int64_t)c.Dh.size() == c.m) {
     std::vector<double> dD(c.m);
     for (int64_t r = 0; r < c.m; ++r) dD[r] = D[r] - c.Dh[r];
-    st = update_hierarchy_contact(c.H, S, c.m > 0 ? &J : nullptr, dD.data(), err);
+    st = update_hierarchy_contact(c.H, &S, c.m > 0 ? &J : nullptr, dD.data(), nullptr, err);
     if (st == AMGF_ERR_NOT_SPD) return fail(st, err);
     rebuilt = st != AMGF_OK;  // pattern mismatch: rebuild below
   }
@@ -819,6 +1006,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   if (c.host_only) return AMGF_OK;
   // ---- device upload
   c.release_device();
+  c.bsr0 = BSR3();
   const int nlev = c.H.nlev();
   c.L.assign(nlev, DLevel());
   // mixed precision needs a coarse level and the 3x3 node-block structure of K
@@ -843,6 +1031,8 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
         if ((st = c.upload(&lv.A.soff, bsr.soff.data(), bsr.nslices + 1))) return st;
         if ((st = c.upload(&lv.A.bci, bsr.bci.data(), (int64_t)bsr.bci.size()))) return st;
         if ((st = c.upload(&lv.A.bv, bsr.v.data(), (int64_t)bsr.v.size()))) return st;
+        std::vector<double>().swap(bsr.v);
+        c.bsr0 = std::move(bsr);  // for in-place updates of the contact rows
       } else if ((st = upload_csr(c, c.H.A[l], lv.A))) {
         return st;
       }
@@ -939,6 +1129,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
     for (int64_t i = 0; i <= c.n; ++i) crp[i] = (int32_t)C.rp[i];
     if ((st = c.upload(&c.c_rp, crp.data(), c.n + 1))) return st;
     if ((st = c.upload(&c.c_ci, C.ci.data(), C.nnz()))) return st;
+    c.c_nnz = C.nnz();
     if ((st = c.upload(&c.c_v, C.v.data(), C.nnz()))) return st;
   }
   if (c.F.nc > 0) {
@@ -947,6 +1138,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       if (2 * c.F.nb * (int64_t)sizeof(double) > 200 * 1024)
         return fail(AMGF_ERR_INVALID_ARG, "filter block too large for shared memory");
       if ((st = c.upload(&c.fM, c.F.M.data(), (int64_t)c.F.M.size()))) return st;
+      c.fM_count = (int64_t)c.F.M.size();
       if ((st = c.upload(&c.ftasks, c.F.tasks.data(), (int64_t)c.F.tasks.size()))) return st;
       std::vector<double>().swap(c.F.M);  // the device copy is the only one used
       if (2 * c.F.nb * (int64_t)sizeof(double) > 48 * 1024) {
@@ -1092,6 +1284,7 @@ int amgf_options_default(amgf_options* o) {
   o->filter_algo = 0;
   o->interp = 0;
   o->p_max = 4;
+  o->update_in_place = 1;
   return AMGF_OK;
 }
 
@@ -1117,7 +1310,7 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
   if (opt.nu < 1 || opt.max_levels < 1 || opt.max_coarse < 1 || opt.num_functions < 1 || !(opt.rtol > 0.0) ||
       opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2 || opt.precision < 0 ||
       opt.precision > 3 || opt.filter_algo < 0 || opt.filter_algo > 1 ||
-      opt.interp < 0 || opt.interp > 1 || opt.p_max < 0)
+      opt.interp < 0 || opt.interp > 1 || opt.p_max < 0 || opt.update_in_place < 0 || opt.update_in_place > 1)
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");

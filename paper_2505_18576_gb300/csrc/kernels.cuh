@@ -351,6 +351,13 @@ __global__ void __launch_bounds__(TPB) bsr3_mixed_kernel(Bsr3MixedArgs<VT> a) {
 // (dense_rows_kernel, FP64 or FP32).
 constexpr int DENSE_TPB = 1024;
 
+// out[idx[k]] = val[k] (values of an updated operator written into its device image)
+template <typename T>
+__global__ void scatter_kernel(int64_t n, const int64_t* __restrict__ idx, const T* __restrict__ val, T* out) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[idx[k]] = val[k];
+}
+
 // x_i += W_i * res_i in FP32 (extra sweeps when nu > 1)
 __global__ void axpy_w_f32_kernel(int64_t n, const float* __restrict__ winv, const float* __restrict__ res, float* x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

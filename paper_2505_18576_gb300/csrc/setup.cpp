@@ -628,19 +628,29 @@ bool build_bsr3(const HCSR& A, double max_fill, BSR3& out) {
         if (I >= nb) continue;
         block_cols(I, cols);
         for (size_t j = 0; j < cols.size(); ++j) out.bci[s0 + BSR3::W * j + lane] = cols[j];
-        for (int r = 0; r < 3; ++r) {
-          size_t b = 0;
-          for (int64_t k = A.rp[3 * I + r]; k < A.rp[3 * I + r + 1]; ++k) {
-            const int32_t J = A.ci[k] / 3;
-            while (cols[b] < J) ++b;
-            const int c = A.ci[k] % 3;
-            out.v[9 * s0 + (9 * (int64_t)b + 3 * r + c) * BSR3::W + lane] = A.v[k];
-          }
-        }
       }
+      bsr3_fill_slice(A, out, sl, out.v.data() + 9 * s0);
     }
   }
   return true;
+}
+
+void bsr3_fill_slice(const HCSR& A, const BSR3& L, int64_t sl, double* out) {
+  const int64_t s0 = L.soff[sl], w = (L.soff[sl + 1] - s0) / BSR3::W;
+  std::fill(out, out + 9 * BSR3::W * w, 0.0);
+  for (int lane = 0; lane < BSR3::W; ++lane) {
+    const int64_t I = sl * BSR3::W + lane;
+    if (I >= L.nbrows) continue;
+    for (int r = 0; r < 3; ++r) {
+      int64_t b = 0;  // the row's block columns ascend with j, as its entries do
+      for (int64_t k = A.rp[3 * I + r]; k < A.rp[3 * I + r + 1]; ++k) {
+        const int32_t J = A.ci[k] / 3;
+        while (L.bci[s0 + BSR3::W * b + lane] < J) ++b;
+        const int c = A.ci[k] % 3;
+        out[(9 * b + 3 * r + c) * BSR3::W + lane] = A.v[k];
+      }
+    }
+  }
 }
 
 int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& err) {
@@ -667,8 +677,17 @@ int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& 
   return AMGF_OK;
 }
 
-int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, std::string& err) {
-  const int64_t n = K->nrows;
+namespace {
+// Contact part of S row by row: for every DOF a with a nonzero column of J (ascending in
+// crows), the columns b (ascending) and sums sum_r J_ra D_r J_rb over the constraints r of a,
+// each sum in ascending r and ascending position within row r of J.
+struct ContactRows {
+  std::vector<int64_t> crows;
+  std::vector<std::vector<int32_t>> ccol;
+  std::vector<std::vector<double>> cacc;
+};
+
+int contact_rows(int64_t n, const amgf_csr* J, const double* D, ContactRows& cr, std::string& err) {
   const int64_t m = J ? J->nrows : 0;
   for (int64_t r = 0; r < m; ++r) {
     if (!std::isfinite(D[r])) { err = "D has a non-finite entry"; return AMGF_ERR_NONFINITE; }
@@ -691,21 +710,19 @@ int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, s
         cval[p] = J->val[k];
       }
   }
-  // Rows without a contact column are copied from K; the (few) contact rows are merged.
-  // Two passes: row lengths, then values written in place.
-  std::vector<int64_t> crows;  // rows a with a nonzero column of J
+  cr.crows.clear();
   for (int64_t a = 0; a < n; ++a)
-    if (crp[a + 1] > crp[a]) crows.push_back(a);
-  std::vector<std::vector<int32_t>> ccol(crows.size());
-  std::vector<std::vector<double>> cacc(crows.size());
+    if (crp[a + 1] > crp[a]) cr.crows.push_back(a);
+  cr.ccol.assign(cr.crows.size(), {});
+  cr.cacc.assign(cr.crows.size(), {});
 #pragma omp parallel
   {
     std::vector<double> acc(n, 0.0);
     std::vector<int64_t> mark(n, -1);
     std::vector<int32_t> cols;
 #pragma omp for schedule(dynamic, 64)
-    for (int64_t q = 0; q < (int64_t)crows.size(); ++q) {
-      const int64_t a = crows[q];
+    for (int64_t q = 0; q < (int64_t)cr.crows.size(); ++q) {
+      const int64_t a = cr.crows[q];
       cols.clear();
       for (int64_t k = crp[a]; k < crp[a + 1]; ++k) {
         const int64_t r = crow[k];
@@ -718,24 +735,37 @@ int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, s
         }
       }
       std::sort(cols.begin(), cols.end());
-      ccol[q] = cols;
-      cacc[q].resize(cols.size());
-      for (size_t u = 0; u < cols.size(); ++u) cacc[q][u] = acc[cols[u]];
+      cr.ccol[q] = cols;
+      cr.cacc[q].resize(cols.size());
+      for (size_t u = 0; u < cols.size(); ++u) cr.cacc[q][u] = acc[cols[u]];
     }
   }
-  // merge of row a of K with contact row q (K value first, contact sum added to it); emit(j, v)
-  auto merge = [&](int64_t a, int64_t q, auto&& emit) {
-    int64_t p = K->row_ptr[a], pe = K->row_ptr[a + 1];
-    const std::vector<int32_t>& cols = ccol[q];
-    size_t u = 0;
-    while (p < pe || u < cols.size()) {
-      if (u >= cols.size() || (p < pe && K->col_idx[p] < cols[u])) { emit(K->col_idx[p], K->val[p]); ++p; }
-      else if (p >= pe || cols[u] < K->col_idx[p]) { emit(cols[u], cacc[q][u]); ++u; }
-      else { emit(K->col_idx[p], K->val[p] + cacc[q][u]); ++p; ++u; }
-    }
-  };
+  return AMGF_OK;
+}
+
+// merge of row a of K with contact row q (K value first, contact sum added to it); emit(j, v)
+template <typename Emit>
+void merge_row(const amgf_csr* K, const ContactRows& cr, int64_t a, int64_t q, Emit&& emit) {
+  int64_t p = K->row_ptr[a], pe = K->row_ptr[a + 1];
+  const std::vector<int32_t>& cols = cr.ccol[q];
+  size_t u = 0;
+  while (p < pe || u < cols.size()) {
+    if (u >= cols.size() || (p < pe && K->col_idx[p] < cols[u])) { emit(K->col_idx[p], K->val[p]); ++p; }
+    else if (p >= pe || cols[u] < K->col_idx[p]) { emit(cols[u], cr.cacc[q][u]); ++u; }
+    else { emit(K->col_idx[p], K->val[p] + cr.cacc[q][u]); ++p; ++u; }
+  }
+}
+}  // namespace
+
+int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, std::string& err) {
+  const int64_t n = K->nrows;
+  ContactRows cr;
+  int st = contact_rows(n, J, D, cr, err);
+  if (st) return st;
+  // Rows without a contact column are copied from K; the (few) contact rows are merged.
+  // Two passes: row lengths, then values written in place.
   std::vector<int64_t> qof(n, -1);
-  for (int64_t q = 0; q < (int64_t)crows.size(); ++q) qof[crows[q]] = q;
+  for (int64_t q = 0; q < (int64_t)cr.crows.size(); ++q) qof[cr.crows[q]] = q;
   S.nrows = S.ncols = n;
   S.rp.assign(n + 1, 0);
 #pragma omp parallel for schedule(static)
@@ -743,7 +773,7 @@ int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, s
     int64_t len = K->row_ptr[a + 1] - K->row_ptr[a];
     if (qof[a] >= 0) {
       len = 0;
-      merge(a, qof[a], [&](int32_t, double) { ++len; });
+      merge_row(K, cr, a, qof[a], [&](int32_t, double) { ++len; });
     }
     S.rp[a + 1] = len;
   }
@@ -757,9 +787,33 @@ int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, s
       std::copy(K->col_idx + K->row_ptr[a], K->col_idx + K->row_ptr[a + 1], S.ci.begin() + o);
       std::copy(K->val + K->row_ptr[a], K->val + K->row_ptr[a + 1], S.v.begin() + o);
     } else {
-      merge(a, qof[a], [&](int32_t j, double v) { S.ci[o] = j; S.v[o] = v; ++o; });
+      merge_row(K, cr, a, qof[a], [&](int32_t j, double v) { S.ci[o] = j; S.v[o] = v; ++o; });
     }
   }
+  return AMGF_OK;
+}
+
+int refresh_contact_rows(HCSR& S, const amgf_csr* K, const amgf_csr* J, const double* D,
+                         std::vector<int64_t>& rows, std::string& err) {
+  const int64_t n = K->nrows;
+  ContactRows cr;
+  int st = contact_rows(n, J, D, cr, err);
+  if (st) return st;
+  bool same = S.nrows == n;
+  for (int64_t q = 0; same && q < (int64_t)cr.crows.size(); ++q) {
+    const int64_t a = cr.crows[q];
+    int64_t o = S.rp[a];
+    merge_row(K, cr, a, q, [&](int32_t j, double) { same = same && o < S.rp[a + 1] && S.ci[o] == j; ++o; });
+    same = same && o == S.rp[a + 1];
+  }
+  if (!same) { err = "contact rows changed their pattern"; return AMGF_ERR_INVALID_ARG; }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < (int64_t)cr.crows.size(); ++q) {
+    const int64_t a = cr.crows[q];
+    int64_t o = S.rp[a];
+    merge_row(K, cr, a, q, [&](int32_t, double v) { S.v[o++] = v; });
+  }
+  rows = cr.crows;
   return AMGF_OK;
 }
 
@@ -826,9 +880,11 @@ int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::str
   return AMGF_OK;
 }
 
-int update_hierarchy_contact(Hierarchy& H, const HCSR& S, const amgf_csr* J, const double* dD, std::string& err) {
+int update_hierarchy_contact(Hierarchy& H, const HCSR* S, const amgf_csr* J, const double* dD,
+                             std::vector<std::vector<int64_t>>* changed, std::string& err) {
   const int nlev = H.nlev();
-  H.A[0] = S;
+  if (S) H.A[0] = *S;
+  if (changed) changed->assign(nlev, {});
   if (J && J->nrows > 0 && nlev >= 2) {
     // dA_0 = J^T diag(dD) J
     HCSR Jh;
@@ -844,6 +900,8 @@ int update_hierarchy_contact(Hierarchy& H, const HCSR& S, const amgf_csr* J, con
     for (int l = 0; l + 1 < nlev; ++l) {
       HCSR dAc = spgemm(H.R[l], spgemm(dA, H.P[l]));
       HCSR& Ac = H.A[l + 1];
+      // positions of the entries of dAc in Ac (dAc's pattern must lie inside Ac's)
+      std::vector<int64_t> where(dAc.nnz(), -1);
       bool ok = true;
 #pragma omp parallel for schedule(dynamic, 256) reduction(&& : ok)
       for (int64_t i = 0; i < dAc.nrows; ++i) {
@@ -851,10 +909,13 @@ int update_hierarchy_contact(Hierarchy& H, const HCSR& S, const amgf_csr* J, con
         for (int64_t k = dAc.rp[i]; k < dAc.rp[i + 1]; ++k) {
           while (p < Ac.rp[i + 1] && Ac.ci[p] < dAc.ci[k]) ++p;
           if (p == Ac.rp[i + 1] || Ac.ci[p] != dAc.ci[k]) { ok = false; break; }
-          Ac.v[p] += dAc.v[k];
+          where[k] = p;
         }
       }
       if (!ok) { err = "contact update outside the coarse pattern"; return AMGF_ERR_INVALID_ARG; }
+#pragma omp parallel for schedule(static)
+      for (int64_t k = 0; k < dAc.nnz(); ++k) Ac.v[where[k]] += dAc.v[k];
+      if (changed) (*changed)[l + 1] = std::move(where);
       dA = std::move(dAc);
     }
   }

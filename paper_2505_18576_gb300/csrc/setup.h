@@ -82,6 +82,10 @@ struct BSR3 {
 // below `max_fill` (9 x blocks / nnz); returns false otherwise.
 bool build_bsr3(const HCSR& A, double max_fill, BSR3& out);
 
+// Values of slice sl of A in the layout L (soff, bci, nbrows of an earlier build_bsr3 of a
+// matrix with A's pattern): 9 * 32 * w_sl doubles in the order of BSR3::v from out on.
+void bsr3_fill_slice(const HCSR& A, const BSR3& L, int64_t sl, double* out);
+
 // Input validation; returns an amgf_status.
 int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& err);
 
@@ -89,11 +93,20 @@ int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& 
 // added to K_ab after it.
 int assemble_S(const amgf_csr* K, const amgf_csr* J, const double* D, HCSR& S, std::string& err);
 
-// New contact term for a hierarchy built earlier (interpolation reused): A_0 = S and
-// A_{l+1} += R_l dA_l P_l with dA_0 = J^T diag(dD) J, dD = D_new - D_old, so that every A_l is
-// again the Galerkin operator of the new A for the old P; l1 sums and the coarsest inverse
-// are recomputed.  AMGF_ERR_INVALID_ARG if an update falls outside a coarse pattern.
-int update_hierarchy_contact(Hierarchy& H, const HCSR& S, const amgf_csr* J, const double* dD, std::string& err);
+// The rows of an assembled S = K + J^T D_old J that J touches, rewritten for a new D with
+// the arithmetic of assemble_S (same bits as a fresh assembly); rows = those DOFs, ascending.
+// AMGF_ERR_INVALID_ARG if S's pattern is not the one assemble_S gives.
+int refresh_contact_rows(HCSR& S, const amgf_csr* K, const amgf_csr* J, const double* D,
+                         std::vector<int64_t>& rows, std::string& err);
+
+// New contact term for a hierarchy built earlier (interpolation reused): A_0 = *S (when S is
+// given; else A_0 already holds the new operator) and A_{l+1} += R_l dA_l P_l with
+// dA_0 = J^T diag(dD) J, dD = D_new - D_old, so that every A_l is again the Galerkin operator
+// of the new A for the old P; l1 sums and the coarsest inverse are recomputed.  changed
+// (optional) receives, per level l >= 1, the positions in A_l.v that the update touched.
+// AMGF_ERR_INVALID_ARG if an update falls outside a coarse pattern.
+int update_hierarchy_contact(Hierarchy& H, const HCSR* S, const amgf_csr* J, const double* dD,
+                             std::vector<std::vector<int64_t>>* changed, std::string& err);
 
 // A += diag(E) (E finite, >= 0, length A.nrows): entries are added to stored diagonal
 // entries, and a diagonal entry is inserted (in column order) where a row has none and

@@ -65,3 +65,42 @@ def test_lagged_update(precision):
           f"A-norm diff {ea:.2e}")
     assert st.converged == 1 and ea <= max(4e-8 * np.sqrt(kap), 10 * floor)
     s.close()
+
+
+@pytest.mark.parametrize("precision,filter_algo,learned", [(0, 0, False), (3, 0, True), (0, 1, False), (2, 0, False)])
+def test_in_place_update_equals_full_upload(precision, filter_algo, learned):
+    # amgf_update_D_fine writing new values into the device image (default) and rebuilding the
+    # image (update_in_place = 0) give the same preconditioner and the same solve, bit for bit,
+    # over two successive updates (the second one from an in-place image)
+    import paper_2505_18576_gb300 as m
+    p = cg.make_problem(None, seed=8, nx=16, ny=12, nz=7, d_lo=-2, d_hi=6)
+    Ds = [cg.draw_D_b(s_, p.m, p.n, -2.0, 10.0)[0] for s_ in (81, 82)]
+    opts = dict(precision=precision, filter_algo=filter_algo, max_coarse=128)
+    a = m.Solver(p.K, p.J, p.D, update_in_place=1, **opts)
+    b = m.Solver(p.K, p.J, p.D, update_in_place=0, **opts)
+    if learned:
+        import os
+        from paper_2505_18576_gb300.learned import load_weights
+        w = load_weights(os.path.join(os.path.dirname(m.__file__), "weights", "smoother_c64.npz"))
+        a.set_mlp(w)
+        b.set_mlp(w)
+    r = dev(np.random.default_rng(5).standard_normal(p.n))
+    for D in Ds:
+        a.update_D(D, keep_coarse=True)
+        b.update_D(D, keep_coarse=True)
+        assert a.info.nlevels == b.info.nlevels >= 3
+        for lev in range(a.info.nlevels):
+            assert (a.export(0, lev) != b.export(0, lev)).nnz == 0
+        za = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        zb = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        a.apply(r, za)
+        b.apply(r, zb)
+        torch.cuda.synchronize()
+        assert torch.equal(za, zb)
+        xa = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        xb = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        sa = a.pcg_solve(dev(p.b), xa)
+        sb = b.pcg_solve(dev(p.b), xb)
+        assert sa.status == 0 and sa.iters == sb.iters and torch.equal(xa, xb)
+    a.close()
+    b.close()

@@ -120,7 +120,7 @@ def test_invalid_inputs(tiny):
     with pytest.raises(amgf.AmgfError) as e:
         amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, precision=4)
     assert e.value.status == 1
-    for bad_opt in (dict(filter_algo=2), dict(interp=2), dict(p_max=-1)):
+    for bad_opt in (dict(filter_algo=2), dict(interp=2), dict(p_max=-1), dict(update_in_place=2)):
         with pytest.raises(amgf.AmgfError) as e:
             amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, **bad_opt)
         assert e.value.status == 1

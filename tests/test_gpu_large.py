@@ -5,11 +5,12 @@ compute at this size (the oracle assembles A = K + J^T D J; its AMG setup is not
   - A x: every row within the dot-product forward error bound 2 gamma_k (|A||x|)_i.
   - PCG solutions (FP64, and FP32 V-cycle with BF16 fine-level K): converged to rtol 1e-8, and
     the Galerkin residual |x^T (b - A x)| / (b^T x) (A from the oracle) below 1e-4, and the two
-    solutions agree in the oracle's A-norm within 1e-3 (a consistency check, not parity: the
-    oracle cannot solve at this size, and 5.2e-4 was measured).  Both quantities sit at the FP64
-    rounding floor of A x, whose entries reach D_max = 1e12: the oracle's own A-norm spread
-    between solves started 1e-10 |b| apart is 3e-8 at D_max = 1e8 and 8e-7 at 1e10 (about
-    D_max^0.7), i.e. ~2e-5 at 1e12; 1e-4 leaves a factor 5.
+    solutions agree in the oracle's A-norm within 8 times the FP64 rounding floor f of this
+    system (and within 1e-3).  f is measured here as the A-norm distance between the FP64
+    solve and the same solve started 1e-10 |b| away from zero: with entries of A up to
+    D_max = 1e12 the true residual stalls near u |A||x|, so solves that are equal in exact
+    arithmetic differ by about f (2.9e-4 at c160); the oracle cannot solve at this size, so
+    this is a consistency check, not parity.
 """
 import numpy as np
 import pytest
@@ -60,8 +61,15 @@ def test_c160_matvec_and_solves(c160):
         assert st.status == 0 and st.converged == 1
         assert gal <= 1e-4
         xs[prec] = xh
+        if prec == 0:
+            x2 = (1e-10 * b.abs()).contiguous()
+            s.pcg_solve(b, x2)
+            xs["restart"] = x2.cpu().numpy()
         s.close()
-    d = xs[0] - xs[2]
-    ea = np.sqrt(abs(d @ o.S_apply(d))) / np.sqrt(xs[0] @ o.S_apply(xs[0]))
-    print(f"c160 fp64 vs mixed A-norm diff {ea:.2e}")
-    assert ea <= 1e-3
+    def a_dist(u, v):
+        d = u - v
+        return np.sqrt(abs(d @ o.S_apply(d))) / np.sqrt(v @ o.S_apply(v))
+    floor = a_dist(xs["restart"], xs[0])
+    ea = a_dist(xs[2], xs[0])
+    print(f"c160 fp64 vs mixed A-norm diff {ea:.2e}, FP64 rounding floor {floor:.2e}")
+    assert ea <= 1e-3 and ea <= 8 * floor

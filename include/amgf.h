@@ -61,7 +61,8 @@ typedef struct {
   int max_levels;         /* AMG levels including the coarsest (25) */
   int max_coarse;         /* stop coarsening at n_l <= max_coarse (1200); coarsest solved exactly */
   int num_functions;      /* unknowns per node for the unknown approach (3); DOF i has function i % 3 */
-  int nu;                 /* l1-Jacobi sweeps before and after the coarse correction (1) */
+  int nu;                 /* l1-Jacobi sweeps before and after the coarse correction, or the
+                             degree of the Chebyshev smoother (1) */
   int filter;             /* 1: AMGF (default); 0: plain AMG V-cycle, M = B */
   int contact_components; /* 0: I_c = nonzero columns of J; 1: all num_functions DOFs of those nodes;
                              2: all DOFs (P = I, test) */
@@ -91,6 +92,14 @@ typedef struct {
   int update_in_place;    /* 1 (default): amgf_update_D_fine writes the new values into the
                              device image (same arrays, same solve graph); 0: it rebuilds and
                              uploads the whole image, as amgf_update_D does */
+  int smoother;           /* 0 (default): l1-Jacobi, nu sweeps x += W (b - A x), W = 1/l1;
+                             1: Chebyshev polynomial of degree nu in W A for the interval
+                             [cheby_lower, 1] (the l1 sums bound the spectrum of W A by 1), by the
+                             three-term recurrence of Chebyshev acceleration; the same polynomial
+                             before and after the coarse correction keeps B symmetric.  One
+                             residual pass plus one vector update per degree.  Learned weights
+                             (amgf_set_mlp) apply to smoother 0 only. */
+  double cheby_lower;     /* lower end of the Chebyshev interval, in (0, 1) (0.3) */
 } amgf_options;
 
 typedef struct {

@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("num_functions", ctypes.c_int),
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int),
                 ("contact_components", ctypes.c_int), ("build_amg", ctypes.c_int),
-                ("interp", ctypes.c_int), ("p_max", ctypes.c_int)]
+                ("interp", ctypes.c_int), ("p_max", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("cheby_lower", ctypes.c_double)]
 
 
 def _load():

@@ -40,7 +40,9 @@
  *               of constants) is unchanged; a row whose kept weights sum to zero is left whole.
  *   Galerkin  : R = P^T, A_c = R (A P); every sum taken in ascending index order
  *   smoother  : nu sweeps of x <- x + (r - A x) / l1, l1_i = sum_j |a_ij|, zero start on the way
- *               down and the same sweeps on the way up (B symmetric)
+ *               down and the same sweeps on the way up (B symmetric); smoother = 1: the
+ *               Chebyshev polynomial of degree nu in W A = diag(1/l1) A for [cheby_lower, 1]
+ *               instead, the same polynomial down and up
  *   coarsest  : dense Cholesky when n_l <= max_coarse (or coarsening stalls)
  *   filter    : A_w factored by banded Cholesky after a reverse Cuthill-McKee ordering (exact solve)
  *
@@ -80,6 +82,8 @@ typedef struct {
   int build_amg;         /* 1: full setup; 0: assemble A only (for A x on large problems) */
   int interp;            /* 0: classical interpolation (default); 1: direct interpolation */
   int p_max;             /* interpolation truncation: at most p_max weights per F row (4; 0: none) */
+  int smoother;          /* 0: l1-Jacobi (nu sweeps); 1: Chebyshev of degree nu in W A */
+  double cheby_lower;    /* Chebyshev: the polynomial damps eigenvalues of W A in [cheby_lower, 1] */
 } orc_opts;
 
 typedef struct {
@@ -577,6 +581,36 @@ static int amg_setup(orc_t* h) {
 }
 
 /* x = B_l r  (V-cycle, recursive) */
+/* Chebyshev smoothing of A x = b with the l1-scaled operator W A, W = diag(1 / l1): its
+ * eigenvalues lie in (0, 1] (l1 row sums bound the spectrum), and the polynomial is the
+ * shifted Chebyshev polynomial of the interval [lo, 1], applied by the three-term recurrence
+ * of Chebyshev acceleration (Saad, Iterative Methods for Sparse Linear Systems, Algorithm
+ * 12.1) with centre c = (1 + lo) / 2, half-width h = (1 - lo) / 2, s = c / h:
+ *   rho_0 = 1 / s,  d_0 = W r_0 / c,  x_1 = x_0 + d_0,
+ *   rho_j = 1 / (2 s - rho_{j-1}),  d_j = rho_j rho_{j-1} d_{j-1} + (2 rho_j / h) W r_j,
+ *   x_{j+1} = x_j + d_j,  r_j = b - A x_j.
+ * k steps leave the error q_k(W A) e_0, q_k(l) = T_k((c - l) / h) / T_k(s).  from_zero: x_0 = 0
+ * (r_0 = b, no product). */
+static void cheby_smooth(const ocsr* A, const double* l1, const double* b, double* x, int k, double lo,
+                         int from_zero, double* res, double* d) {
+  const int64_t n = A->nrows;
+  const double c = 0.5 * (1.0 + lo), hw = 0.5 * (1.0 - lo), sg = c / hw;
+  double rho = 1.0 / sg;
+  if (from_zero) {
+    for (int64_t i = 0; i < n; ++i) { d[i] = (b[i] / l1[i]) / c; x[i] = d[i]; }
+  } else {
+    csr_resid(A, b, x, res);
+    for (int64_t i = 0; i < n; ++i) { d[i] = (res[i] / l1[i]) / c; x[i] += d[i]; }
+  }
+  for (int j = 1; j < k; ++j) {
+    const double rho_new = 1.0 / (2.0 * sg - rho);
+    const double a = rho_new * rho, bc = 2.0 * rho_new / hw;
+    csr_resid(A, b, x, res);
+    for (int64_t i = 0; i < n; ++i) { d[i] = a * d[i] + bc * (res[i] / l1[i]); x[i] += d[i]; }
+    rho = rho_new;
+  }
+}
+
 static void vcycle(orc_t* h, int l, const double* r, double* x) {
   orc_amg* g = &h->amg;
   const ocsr* A = &g->A[l];
@@ -585,11 +619,17 @@ static void vcycle(orc_t* h, int l, const double* r, double* x) {
   const double* l1 = g->l1[l];
   const double* th = g->theta[l];
   double* res = xmalloc(n * sizeof(double));
-  /* pre-smoothing from x = 0: x = W r, W = diag(theta / l1) (theta = 1 without weights) */
-  for (int64_t i = 0; i < n; ++i) x[i] = th ? (th[i] / l1[i]) * r[i] : r[i] / l1[i];
-  for (int s = 1; s < h->o.nu; ++s) {
-    csr_resid(A, r, x, res);
-    for (int64_t i = 0; i < n; ++i) x[i] += th ? (th[i] / l1[i]) * res[i] : res[i] / l1[i];
+  const int cheb = h->o.smoother == 1;
+  double* d = cheb ? xmalloc(n * sizeof(double)) : NULL;
+  if (cheb) {
+    cheby_smooth(A, l1, r, x, h->o.nu, h->o.cheby_lower, 1, res, d);
+  } else {
+    /* pre-smoothing from x = 0: x = W r, W = diag(theta / l1) (theta = 1 without weights) */
+    for (int64_t i = 0; i < n; ++i) x[i] = th ? (th[i] / l1[i]) * r[i] : r[i] / l1[i];
+    for (int s = 1; s < h->o.nu; ++s) {
+      csr_resid(A, r, x, res);
+      for (int64_t i = 0; i < n; ++i) x[i] += th ? (th[i] / l1[i]) * res[i] : res[i] / l1[i];
+    }
   }
   /* coarse-grid correction */
   csr_resid(A, r, x, res);
@@ -601,12 +641,16 @@ static void vcycle(orc_t* h, int l, const double* r, double* x) {
   double* pe = xmalloc(n * sizeof(double));
   csr_mv(&g->P[l], ec, pe);
   for (int64_t i = 0; i < n; ++i) x[i] += pe[i];
-  /* post-smoothing (same W as before the coarse correction, so B stays symmetric) */
-  for (int s = 0; s < h->o.nu; ++s) {
-    csr_resid(A, r, x, res);
-    for (int64_t i = 0; i < n; ++i) x[i] += th ? (th[i] / l1[i]) * res[i] : res[i] / l1[i];
+  /* post-smoothing (the same smoother as before the coarse correction, so B stays symmetric) */
+  if (cheb) {
+    cheby_smooth(A, l1, r, x, h->o.nu, h->o.cheby_lower, 0, res, d);
+  } else {
+    for (int s = 0; s < h->o.nu; ++s) {
+      csr_resid(A, r, x, res);
+      for (int64_t i = 0; i < n; ++i) x[i] += th ? (th[i] / l1[i]) * res[i] : res[i] / l1[i];
+    }
   }
-  free(res); free(rc); free(ec); free(pe);
+  free(res); free(rc); free(ec); free(pe); free(d);
 }
 
 /* ------------------------------------------------------------------ */
@@ -770,6 +814,8 @@ void orc_opts_default(orc_opts* o) {
   o->build_amg = 1;
   o->interp = 0;
   o->p_max = 4;
+  o->smoother = 0;
+  o->cheby_lower = 0.3;
 }
 
 const char* orc_error(orc_t* h) { return h ? h->err : "null handle"; }
@@ -801,6 +847,8 @@ int orc_create_bounds(int64_t n,
                       const double* D, const double* E, const orc_opts* opts, orc_t** out) {
   *out = NULL;
   if (n <= 0 || m < 0) return ORC_INVALID;
+  if (opts->smoother < 0 || opts->smoother > 1 || !(opts->cheby_lower > 0.0 && opts->cheby_lower < 1.0))
+    return ORC_INVALID;
   orc_t* h = xcalloc(1, sizeof(orc_t));
   h->o = *opts;
   h->n = n; h->m = m;

@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int), ("contact_components", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("precision", ctypes.c_int), ("filter_algo", ctypes.c_int),
-                ("interp", ctypes.c_int), ("p_max", ctypes.c_int), ("update_in_place", ctypes.c_int)]
+                ("interp", ctypes.c_int), ("p_max", ctypes.c_int), ("update_in_place", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("cheby_lower", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

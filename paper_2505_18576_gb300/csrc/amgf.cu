@@ -78,12 +78,38 @@ struct DLevel {
   DCSR A, P, R;
   double* winv = nullptr;
   double *rhs = nullptr, *x = nullptr, *res = nullptr, *out = nullptr;
+  double* d = nullptr;  // Chebyshev smoother: direction of the recurrence
   // FP32 copies used when the V-cycle runs in single precision
   DCSRf Af, Pf, Rf;
   float* winvf = nullptr;
   float *rhsf = nullptr, *xf = nullptr, *resf = nullptr, *outf = nullptr;
+  float* df = nullptr;
   int64_t n = 0;
 };
+
+// Chebyshev smoother of degree k for the interval [lo, 1] of W A (three-term recurrence of
+// Chebyshev acceleration): centre c = (1 + lo)/2, half-width h = (1 - lo)/2, s = c/h; the first
+// step scales W r by 1/c, step j >= 1 uses d = a_j d + bc_j W r with rho_0 = 1/s,
+// rho_j = 1/(2 s - rho_{j-1}), a_j = rho_j rho_{j-1}, bc_j = 2 rho_j / h.
+struct ChebCoefs {
+  double inv_c = 1.0;
+  std::vector<double> a, bc;  // index j = 1 .. k-1 (entry 0 unused)
+};
+static ChebCoefs cheb_coefs(double lo, int k) {
+  ChebCoefs r;
+  const double cc = 0.5 * (1.0 + lo), hw = 0.5 * (1.0 - lo), sg = cc / hw;
+  r.inv_c = 1.0 / cc;
+  r.a.assign(k, 0.0);
+  r.bc.assign(k, 0.0);
+  double rho = 1.0 / sg;
+  for (int j = 1; j < k; ++j) {
+    const double rn = 1.0 / (2.0 * sg - rho);
+    r.a[j] = rn * rho;
+    r.bc[j] = 2.0 * rn / hw;
+    rho = rn;
+  }
+  return r;
+}
 
 struct Ctx {
   amgf_options o{};
@@ -364,15 +390,25 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
                            double* dotres) {
   const int nlev = (int)c.L.size();
   const int nu = c.o.nu < 1 ? 1 : c.o.nu;
+  const bool cheb = c.o.smoother == 1;
+  const ChebCoefs cf = cheb_coefs(c.o.cheby_lower, nu);
   auto rhs_of = [&](int l) -> const double* { return l == 0 ? rhs0 : c.L[l].rhs; };
   for (int l = 0; l + 1 < nlev; ++l) {
     DLevel& lv = c.L[l];
     // pre-smoothing from zero: x = W r (already in lv.x); residual r - A x
+    if (cheb) {
+      cheb_init_kernel<double><<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.x, lv.d, cf.inv_c);
+      c.launches++;
+    }
     CsrArgs a{};
     a.x = lv.x; a.b = rhs_of(l); a.y = lv.res;
     launch_csr<M_RESID>(c, lv.A, a);
     for (int s = 1; s < nu; ++s) {
-      axpy_w_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.x);
+      if (cheb)
+        cheb_step_kernel<double, false><<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.d, lv.x,
+                                                                           cf.a[s], cf.bc[s]);
+      else
+        axpy_w_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.x);
       c.launches++;
       CsrArgs rr{};
       rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
@@ -404,6 +440,34 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
     CsrArgs pa{};
     pa.x = c.L[l + 1].out; pa.y = lv.x;
     launch_csr<M_SPMV_ADD>(c, lv.P, pa);
+    if (cheb) {
+      double* out = l == 0 ? out0 : lv.out;
+      const double* add = l == 0 ? add0 : nullptr;
+      const bool dot = l == 0 && dotres;
+      const int g = vec_grid(c, lv.n);
+      for (int j = 0; j < nu; ++j) {
+        CsrArgs rr{};
+        rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
+        launch_csr<M_RESID>(c, lv.A, rr);
+        const double aj = j ? cf.a[j] : 0.0, bj = j ? cf.bc[j] : cf.inv_c;
+        if (j + 1 < nu) {
+          if (j == 0) cheb_step_kernel<double, true><<<g, TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.d, lv.x, aj, bj);
+          else cheb_step_kernel<double, false><<<g, TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.d, lv.x, aj, bj);
+        } else {
+          auto go = [&](auto first, auto withdot) {
+            cheb_out_kernel<double, double, decltype(first)::value, decltype(withdot)::value><<<g, TPB, 0, c.s>>>(
+                lv.n, lv.winv, lv.res, lv.d, lv.x, aj, bj, add, out, dotv, c.partial, dotres, c.counter);
+          };
+          if (j == 0) {
+            if (dot) go(std::true_type{}, std::true_type{}); else go(std::true_type{}, std::false_type{});
+          } else {
+            if (dot) go(std::false_type{}, std::true_type{}); else go(std::false_type{}, std::false_type{});
+          }
+        }
+        c.launches++;
+      }
+      continue;
+    }
     for (int s = 1; s < nu; ++s) {
       CsrArgs rr{};
       rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
@@ -427,11 +491,21 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
 static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const double* dotv, double* dotres) {
   const int nlev = (int)c.L.size();
   const int nu = c.o.nu < 1 ? 1 : c.o.nu;
+  const bool cheb = c.o.smoother == 1;
+  const ChebCoefs cf = cheb_coefs(c.o.cheby_lower, nu);
   for (int l = 0; l + 1 < nlev; ++l) {
     DLevel& lv = c.L[l];
+    if (cheb) {
+      cheb_init_kernel<float><<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.xf, lv.df, (float)cf.inv_c);
+      c.launches++;
+    }
     for (int s = 0; s < nu; ++s) {
       if (s > 0) {
-        axpy_w_f32_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.xf);
+        if (cheb)
+          cheb_step_kernel<float, false><<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.df, lv.xf,
+                                                                            (float)cf.a[s], (float)cf.bc[s]);
+        else
+          axpy_w_f32_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.xf);
         c.launches++;
       }
       if (l == 0) {
@@ -459,6 +533,46 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
     CsrArgsT<float> pa{};
     pa.x = c.L[l + 1].outf; pa.y = lv.xf;
     launch_csr_f<M_SPMV_ADD>(c, lv.Pf, pa);
+    if (cheb) {
+      const bool dot = l == 0 && dotres;
+      const int g = vec_grid(c, lv.n);
+      for (int j = 0; j < nu; ++j) {
+        if (l == 0) {
+          launch_fine_mixed<M_RESID>(c, lv.xf, lv.rhsf, nullptr, nullptr, lv.resf, nullptr, nullptr, nullptr);
+        } else {
+          CsrArgsT<float> rr{};
+          rr.x = lv.xf; rr.b = lv.rhsf; rr.y = lv.resf;
+          launch_csr_f<M_RESID>(c, lv.Af, rr);
+        }
+        const float aj = j ? (float)cf.a[j] : 0.f, bj = j ? (float)cf.bc[j] : (float)cf.inv_c;
+        if (j + 1 < nu) {
+          if (j == 0) cheb_step_kernel<float, true><<<g, TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.df, lv.xf, aj, bj);
+          else cheb_step_kernel<float, false><<<g, TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.df, lv.xf, aj, bj);
+        } else if (l == 0) {
+          // the fine level's output crosses into the FP64 PCG (+ add0, dot)
+          auto go = [&](auto first, auto withdot) {
+            cheb_out_kernel<float, double, decltype(first)::value, decltype(withdot)::value><<<g, TPB, 0, c.s>>>(
+                lv.n, lv.winvf, lv.resf, lv.df, lv.xf, aj, bj, add0, out0, dotv, c.partial, dotres, c.counter);
+          };
+          if (j == 0) {
+            if (dot) go(std::true_type{}, std::true_type{}); else go(std::true_type{}, std::false_type{});
+          } else {
+            if (dot) go(std::false_type{}, std::true_type{}); else go(std::false_type{}, std::false_type{});
+          }
+        } else {
+          if (j == 0)
+            cheb_out_kernel<float, float, true, false><<<g, TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.df, lv.xf, aj, bj,
+                                                                          nullptr, lv.outf, nullptr, nullptr, nullptr,
+                                                                          nullptr);
+          else
+            cheb_out_kernel<float, float, false, false><<<g, TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.df, lv.xf, aj,
+                                                                           bj, nullptr, lv.outf, nullptr, nullptr,
+                                                                           nullptr, nullptr);
+        }
+        c.launches++;
+      }
+      continue;
+    }
     for (int s = 1; s < nu; ++s) {
       if (l == 0) {
         launch_fine_mixed<M_RESID>(c, lv.xf, lv.rhsf, nullptr, nullptr, lv.resf, nullptr, nullptr, nullptr);
@@ -1047,6 +1161,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       if ((st = c.alloc(&lv.rhs, lv.n))) return st;
       if ((st = c.alloc(&lv.res, lv.n))) return st;
       if ((st = c.alloc(&lv.out, lv.n))) return st;
+      if (c.o.smoother == 1 && (st = c.alloc(&lv.d, lv.n))) return st;
     } else {
       if (l > 0 && (st = upload_csr_f(c, c.H.A[l], lv.Af))) return st;
       if (l + 1 < nlev) {
@@ -1059,6 +1174,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       if ((st = c.alloc(&lv.xf, lv.n))) return st;
       if ((st = c.alloc(&lv.resf, lv.n))) return st;
       if ((st = c.alloc(&lv.outf, lv.n))) return st;
+      if (c.o.smoother == 1 && (st = c.alloc(&lv.df, lv.n))) return st;
     }
   }
   // learned-smoother inputs: features and l1 of every smoothed level
@@ -1285,6 +1401,8 @@ int amgf_options_default(amgf_options* o) {
   o->interp = 0;
   o->p_max = 4;
   o->update_in_place = 1;
+  o->smoother = 0;
+  o->cheby_lower = 0.3;
   return AMGF_OK;
 }
 
@@ -1310,7 +1428,8 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
   if (opt.nu < 1 || opt.max_levels < 1 || opt.max_coarse < 1 || opt.num_functions < 1 || !(opt.rtol > 0.0) ||
       opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2 || opt.precision < 0 ||
       opt.precision > 3 || opt.filter_algo < 0 || opt.filter_algo > 1 ||
-      opt.interp < 0 || opt.interp > 1 || opt.p_max < 0 || opt.update_in_place < 0 || opt.update_in_place > 1)
+      opt.interp < 0 || opt.interp > 1 || opt.p_max < 0 || opt.update_in_place < 0 || opt.update_in_place > 1 || opt.smoother < 0 ||
+      opt.smoother > 1 || !(opt.cheby_lower > 0.0 && opt.cheby_lower < 1.0))
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");
@@ -1548,6 +1667,8 @@ int amgf_set_mlp(amgf_handle h, const float* weights, int64_t nw) {
   if (h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
   Ctx& c = h->c;
   if (weights && nw != MLP_NW) return fail(AMGF_ERR_INVALID_ARG, "the smoother MLP has 1313 weights");
+  if (weights && c.o.smoother != 0)
+    return fail(AMGF_ERR_INVALID_ARG, "learned weights damp the l1-Jacobi smoother (options.smoother = 0)");
   if (weights)
     for (int64_t k = 0; k < nw; ++k)
       if (!std::isfinite(weights[k])) return fail(AMGF_ERR_NONFINITE, "non-finite MLP weight");

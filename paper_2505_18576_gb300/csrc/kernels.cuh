@@ -351,6 +351,47 @@ __global__ void __launch_bounds__(TPB) bsr3_mixed_kernel(Bsr3MixedArgs<VT> a) {
 // (dense_rows_kernel, FP64 or FP32).
 constexpr int DENSE_TPB = 1024;
 
+// Chebyshev smoother (three-term recurrence of Chebyshev acceleration for W A, W = 1/l1):
+// each step follows a RESID pass res = b - A x and applies d = a d + bc W res, x += d (the
+// first step of a sweep from a nonzero x: d = bc W res).  A sweep from zero starts from the
+// producer's x = W b: cheb_init scales it to d = x = W b / c.  The last step of a
+// post-smoothing writes out = x + d [+ add] to the level's output instead of updating x, with
+// an optional dot product of the output.
+template <typename T>
+__global__ void cheb_init_kernel(int64_t n, T* x, T* d, T s) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = x[i] * s;
+    x[i] = v;
+    d[i] = v;
+  }
+}
+
+template <typename T, bool FIRST>
+__global__ void cheb_step_kernel(int64_t n, const T* __restrict__ winv, const T* __restrict__ res, T* d, T* x, T a,
+                                 T bc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = FIRST ? bc * (winv[i] * res[i]) : a * d[i] + bc * (winv[i] * res[i]);
+    d[i] = v;
+    x[i] += v;
+  }
+}
+
+template <typename T, typename TO, bool FIRST, bool DOT>
+__global__ void __launch_bounds__(TPB) cheb_out_kernel(int64_t n, const T* __restrict__ winv, const T* __restrict__ res,
+                                                       const T* __restrict__ d, const T* __restrict__ x, T a, T bc,
+                                                       const double* add, TO* out, const double* dotv,
+                                                       double* partial, double* result, unsigned* counter) {
+  double dacc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = FIRST ? bc * (winv[i] * res[i]) : a * d[i] + bc * (winv[i] * res[i]);
+    double o = (double)(x[i] + v);
+    if (add) o += add[i];
+    out[i] = (TO)o;
+    if (DOT) dacc += dotv[i] * o;
+  }
+  if (DOT) grid_dot_finish(dacc, partial, result, counter);
+}
+
 // out[idx[k]] = val[k] (values of an updated operator written into its device image)
 template <typename T>
 __global__ void scatter_kernel(int64_t n, const int64_t* __restrict__ idx, const T* __restrict__ val, T* out) {

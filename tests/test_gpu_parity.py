@@ -355,3 +355,59 @@ def test_filter_solve_few_blocks(dims):
         assert st.converged == 1 and abs(st.iters - ko) <= 1
         assert np.linalg.norm(host(x) - xo) <= 1e-8 * np.linalg.norm(xo)
         s.close()
+
+
+# ---------------------------------------------------------------- Chebyshev smoother
+@pytest.mark.parametrize("nu,lo", [(2, 0.3), (3, 0.2), (1, 0.3)])
+def test_chebyshev_smoother_parity(nu, lo):
+    # degree-nu Chebyshev smoothing (options.smoother = 1): V-cycle within 1e-12 of the oracle's
+    # recurrence (pinned there against the closed-form polynomial), AMGF apply within the
+    # kappa(A_w) bound, PCG iterations within +-1, on a hierarchy deep enough for every level kind
+    import paper_2505_18576_gb300 as m
+    p = cg.make_problem(None, seed=2, nx=16, ny=12, nz=7, d_lo=-2, d_hi=8)
+    opts = dict(smoother=1, nu=nu, cheby_lower=lo, max_coarse=128, p_max=0)
+    o = oracle.Oracle(p.K, p.J, p.D, **opts)
+    s = m.Solver(p.K, p.J, p.D, **opts)
+    assert s.info.nlevels >= 4
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal(p.n)
+    x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(r), x)
+    xo = o.vcycle(r)
+    assert np.linalg.norm(host(x) - xo) <= 1e-12 * np.linalg.norm(xo)
+    z = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.apply(dev(r), z)
+    zo = o.apply(r)
+    assert np.linalg.norm(host(z) - zo) <= kappa_tol(o) * np.linalg.norm(zo)
+    xo2, ko, sto, *_ = o.pcg(p.b, tol=1e-8)
+    xs = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(dev(p.b), xs)
+    print(f"chebyshev degree {nu}, lower {lo}: {st.iters} iterations (oracle {ko})")
+    assert sto == 0 and st.status == 0 and abs(st.iters - ko) <= 1
+    s.close()
+    o.close()
+
+
+@pytest.mark.parametrize("precision", [1, 3])
+def test_chebyshev_smoother_mixed(precision):
+    # the FP32 / BF16 V-cycle with the Chebyshev smoother against the FP64 oracle's
+    import paper_2505_18576_gb300 as m
+    p = cg.make_problem(None, seed=2, nx=16, ny=12, nz=7, d_lo=-2, d_hi=8)
+    opts = dict(smoother=1, nu=2, max_coarse=128, p_max=0)
+    o = oracle.Oracle(p.K, p.J, p.D, **opts)
+    s = m.Solver(p.K, p.J, p.D, precision=precision, **opts)
+    r = np.random.default_rng(10).standard_normal(p.n)
+    x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s.vcycle(dev(r), x)
+    xo = o.vcycle(r)
+    err = np.linalg.norm(host(x) - xo) / np.linalg.norm(xo)
+    assert err <= (1e-4 if precision == 1 else 5e-2)
+    xs = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    st = s.pcg_solve(dev(p.b), xs)
+    _, ko, *_ = o.pcg(p.b, tol=1e-8)
+    print(f"chebyshev precision {precision}: V-cycle rel diff {err:.2e}, {st.iters} iterations (oracle {ko})")
+    assert st.status == 0 and st.iters <= ko + 3
+    with pytest.raises(m.AmgfError):
+        s.set_mlp(np.zeros(1313, np.float32))  # learned weights belong to the l1-Jacobi smoother
+    s.close()
+    o.close()

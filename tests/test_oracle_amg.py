@@ -201,17 +201,35 @@ def test_strength_is_componentwise(tiny):
         assert np.array_equal(ff[P.row], fc[P.col])
 
 
-def _dense_B(o, l):
+def _cheb_q(A, k, lo):
+    # closed form of the Chebyshev smoother's error propagation: q_k(W A) with
+    # q_k(l) = T_k((c - l) / h) / T_k(c / h), c = (1 + lo) / 2, h = (1 - lo) / 2, W = diag(1/l1),
+    # from the eigen-decomposition of the symmetric W^(1/2) A W^(1/2)
+    from numpy.polynomial import chebyshev as C
+    w = 1.0 / np.abs(A).sum(axis=1)
+    sw = np.sqrt(w)
+    lam, V = np.linalg.eigh(sw[:, None] * A * sw[None, :])
+    c, h = 0.5 * (1 + lo), 0.5 * (1 - lo)
+    Tk = np.zeros(k + 1)
+    Tk[k] = 1.0
+    q = C.chebval((c - lam) / h, Tk) / C.chebval(c / h, Tk)
+    return sw[:, None] * (V * q) @ V.T / sw[None, :]
+
+
+def _dense_B(o, l, cheb=None):
     A = o.A(l).toarray()
     if l == o.nlev - 1:
         return np.linalg.inv(A)
     n = A.shape[0]
-    W = np.diag(1.0 / np.abs(A).sum(axis=1))
     P = o.P(l).toarray()
-    Bc = _dense_B(o, l + 1)
+    Bc = _dense_B(o, l + 1, cheb)
     I = np.eye(n)
-    # error propagation of one V(1,1) cycle: (I - W A)(I - P B_c P^T A)(I - W A) = I - B A
-    E = (I - W @ A) @ (I - P @ Bc @ P.T @ A) @ (I - W @ A)
+    if cheb is None:
+        S = I - np.diag(1.0 / np.abs(A).sum(axis=1)) @ A  # one l1-Jacobi sweep
+    else:
+        S = _cheb_q(A, *cheb)
+    # error propagation of one V-cycle: S (I - P B_c P^T A) S = I - B A
+    E = S @ (I - P @ Bc @ P.T @ A) @ S
     return (I - E) @ np.linalg.inv(A)
 
 
@@ -225,6 +243,31 @@ def test_vcycle_error_propagation_identity(tiny):
         got = o.vcycle(X[:, k])
         ref = Bref @ X[:, k]
         assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("k,lo", [(2, 0.3), (3, 0.3), (2, 0.1)])
+def test_vcycle_chebyshev_closed_form(tiny, k, lo):
+    # the recurrence of the Chebyshev smoother against the closed-form polynomial q_k(W A);
+    # B stays symmetric with eigenvalues of B A in (0, 1]
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, filter=0, max_coarse=128, smoother=1, nu=k, cheby_lower=lo)
+    assert o.nlev >= 3
+    n = tiny.n
+    Bref = _dense_B(o, 0, (k, lo))
+    rng = np.random.default_rng(4)
+    for _ in range(4):
+        x = rng.standard_normal(n)
+        ref = Bref @ x
+        assert np.linalg.norm(o.vcycle(x) - ref) <= 1e-9 * np.linalg.norm(ref)
+    B = np.column_stack([o.vcycle(e) for e in np.eye(n)])
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    L = np.linalg.cholesky(o.S().toarray())
+    ev = np.linalg.eigvalsh(L.T @ B @ L)
+    assert ev.min() > 0 and ev.max() <= 1.0 + 1e-10
+    # degree 1 with lo -> the interval's centre: one sweep x = W b / c
+    o1 = oracle.Oracle(tiny.K, tiny.J, tiny.D, filter=0, max_coarse=128, smoother=1, nu=1, cheby_lower=lo)
+    B1 = _dense_B(o1, 0, (1, lo))
+    x = rng.standard_normal(n)
+    assert np.linalg.norm(o1.vcycle(x) - B1 @ x) <= 1e-9 * np.linalg.norm(B1 @ x)
 
 
 def test_vcycle_symmetric_convergent(tiny):

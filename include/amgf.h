@@ -56,7 +56,7 @@ typedef struct {
 } amgf_csr;
 
 typedef struct {
-  double strength_theta;  /* AMG strength threshold (0.55) */
+  double strength_theta;  /* AMG strength threshold (0.52) */
   double rtol;            /* PCG stop: sqrt(r^T z / r0^T z0) < rtol (1e-8); Section 4 uses this norm */
   int max_levels;         /* AMG levels including the coarsest (25) */
   int max_coarse;         /* stop coarsening at n_l <= max_coarse (1200); coarsest solved exactly */

@@ -72,7 +72,7 @@ typedef struct {
 } ocsr;
 
 typedef struct {
-  double strength_theta; /* 0.8 */
+  double strength_theta; /* 0.52 */
   int max_coarse;        /* 1200 */
   int max_levels;        /* 25 */
   int num_functions;     /* 3: DOF i has function i % 3 on the finest level */
@@ -804,7 +804,7 @@ static void filter_solve(orc_t* h, const double* v, double* w) {
 /* public API                                                          */
 
 void orc_opts_default(orc_opts* o) {
-  o->strength_theta = 0.55;
+  o->strength_theta = 0.52;
   o->max_coarse = 1200;
   o->max_levels = 25;
   o->num_functions = 3;

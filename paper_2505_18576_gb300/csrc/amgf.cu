@@ -1079,7 +1079,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
     const int r = update_D_in_place(c, D, K, J, err);
     if (r == AMGF_OK) return AMGF_OK;
     if (r == kRebuild) keep_coarse = false;
-    else if (r != kFallback) return fail(r, err);
+    else if (r != kFallback) return err.empty() ? r : fail(r, err);  // CUDA errors are reported already
     err.clear();
   }
   HCSR S;
@@ -1385,7 +1385,7 @@ extern "C" {
 int amgf_options_default(amgf_options* o) {
   if (!o) return fail(AMGF_ERR_INVALID_ARG, "null options");
   std::memset(o, 0, sizeof *o);
-  o->strength_theta = 0.55;
+  o->strength_theta = 0.52;
   o->rtol = 1e-8;
   o->max_levels = 25;
   o->max_coarse = 1200;

@@ -120,7 +120,8 @@ def test_invalid_inputs(tiny):
     with pytest.raises(amgf.AmgfError) as e:
         amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, precision=4)
     assert e.value.status == 1
-    for bad_opt in (dict(filter_algo=2), dict(interp=2), dict(p_max=-1), dict(update_in_place=2)):
+    for bad_opt in (dict(filter_algo=2), dict(interp=2), dict(p_max=-1), dict(update_in_place=2), dict(smoother=2),
+                    dict(smoother=1, cheby_lower=1.0), dict(cheby_lower=0.0)):
         with pytest.raises(amgf.AmgfError) as e:
             amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True, **bad_opt)
         assert e.value.status == 1

@@ -305,3 +305,7 @@ def test_invalid_inputs(tiny):
     with pytest.raises(oracle.OracleError) as e:
         oracle.Oracle(tiny.K, tiny.J, D)
     assert e.value.status == 3
+    for bad in (dict(smoother=2), dict(smoother=1, cheby_lower=1.0), dict(cheby_lower=0.0)):
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.Oracle(tiny.K, tiny.J, tiny.D, **bad)
+        assert e.value.status == 1

@@ -1082,22 +1082,40 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
     else if (r != kFallback) return err.empty() ? r : fail(r, err);  // CUDA errors are reported already
     err.clear();
   }
+  // A = K + J^T D J (+ diag(E)): assembled, or (interpolation reused, no bound term) the
+  // contact rows of the current A_0 rewritten in place with the same arithmetic
   HCSR S;
-  int st = assemble_S(&K, c.m > 0 ? &J : nullptr, D, S, err);
-  if (st) return fail(st, err);
+  bool have_S = false;
   const double* E = c.Eh.empty() ? nullptr : c.Eh.data();
-  if (E && (st = add_diagonal(S, E, err))) return fail(st, err);
-  const double t_assemble = since(t_start);
+  auto assemble = [&]() -> int {
+    int r = assemble_S(&K, c.m > 0 ? &J : nullptr, D, S, err);
+    if (!r && E) r = add_diagonal(S, E, err);
+    have_S = r == AMGF_OK;
+    return r;
+  };
+  int st = AMGF_OK;
+  double t_assemble = 0.0;
   auto t1 = std::chrono::steady_clock::now();
   bool rebuilt = true;
-  if (keep_coarse && c.H.nlev() >= 2 && c.H.A[0].nrows == S.nrows && (int64_t)c.Dh.size() == c.m) {
+  if (keep_coarse && c.H.nlev() >= 2 && c.H.A[0].nrows == c.n && (int64_t)c.Dh.size() == c.m) {
     std::vector<double> dD(c.m);
     for (int64_t r = 0; r < c.m; ++r) dD[r] = D[r] - c.Dh[r];
-    st = update_hierarchy_contact(c.H, &S, c.m > 0 ? &J : nullptr, dD.data(), nullptr, err);
+    std::vector<int64_t> rows;
+    st = !E && c.m > 0 ? refresh_contact_rows(c.H.A[0], &K, &J, D, rows, err) : AMGF_ERR_INVALID_ARG;
+    if (st == AMGF_ERR_INVALID_ARG && (st = assemble())) return fail(st, err);
+    if (st) return fail(st, err);
+    t_assemble = since(t_start);
+    t1 = std::chrono::steady_clock::now();
+    st = update_hierarchy_contact(c.H, have_S ? &S : nullptr, c.m > 0 ? &J : nullptr, dD.data(), nullptr, err);
     if (st == AMGF_ERR_NOT_SPD) return fail(st, err);
     rebuilt = st != AMGF_OK;  // pattern mismatch: rebuild below
   }
   if (rebuilt) {
+    if (!have_S && (st = assemble())) return fail(st, err);
+    if (t_assemble == 0.0) {
+      t_assemble = since(t_start);
+      t1 = std::chrono::steady_clock::now();
+    }
     st = build_hierarchy(S, c.o, c.H, err);
     if (st) return fail(st, err);
   }
@@ -1105,7 +1123,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   const double t_hier = since(t1);
   t1 = std::chrono::steady_clock::now();
   if (c.o.filter) {
-    st = build_filter(S, c.m > 0 ? &J : nullptr, c.o, c.F, err);
+    st = build_filter(c.H.A[0], c.m > 0 ? &J : nullptr, c.o, c.F, err);  // A_0 = A
     if (st) return fail(st, err);
   } else {
     c.F = Filter();

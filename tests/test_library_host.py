@@ -167,19 +167,25 @@ def test_host_setup_bounds_matches_oracle_bitwise(tiny):
     s.close()
 
 
-def test_update_D_fine_is_galerkin_for_reused_interpolation(tiny):
-    # amgf_update_D_fine keeps P_l and brings every A_l to R_l A_new P_l (host setup only)
-    D2, _ = cg.draw_D_b(91, tiny.m, tiny.n, -2.0, 9.0)
-    s = amgf.Solver(tiny.K, tiny.J, tiny.D, host_only=True)
+@pytest.mark.parametrize("dims", [(8, 8, 4), (16, 12, 7)])
+def test_update_D_fine_is_galerkin_for_reused_interpolation(dims):
+    # amgf_update_D_fine keeps P_l, rewrites the contact rows of A_0 with the bits of a fresh
+    # assembly, and brings every A_l to R_l A_new P_l (host setup only); two successive updates
+    p = cg.make_problem(None, nx=dims[0], ny=dims[1], nz=dims[2], d_lo=-2, d_hi=8, seed=4)
+    s = amgf.Solver(p.K, p.J, p.D, host_only=True, max_coarse=128)
+    assert s.info.nlevels >= 3
     P_old = [s.export(1, l) for l in range(s.info.nlevels - 1)]
-    s.update_D(D2, keep_coarse=True)
-    o = oracle.Oracle(tiny.K, tiny.J, D2, build_amg=0)
-    A = o.S()
-    assert (s.export(0, 0) != A).nnz == 0
-    for l in range(s.info.nlevels - 1):
-        P = s.export(1, l)
-        assert (P != P_old[l]).nnz == 0
-        A = (P.T @ A @ P).tocsr()
-        Al = s.export(0, l + 1)
-        assert abs(Al - A).max() <= 1e-12 * abs(A).max()
+    for seed in (91, 92):
+        D2, _ = cg.draw_D_b(seed, p.m, p.n, -2.0, 9.0)
+        s.update_D(D2, keep_coarse=True)
+        o = oracle.Oracle(p.K, p.J, D2, build_amg=0)
+        A = o.S()
+        assert (s.export(0, 0) != A).nnz == 0
+        for l in range(s.info.nlevels - 1):
+            P = s.export(1, l)
+            assert (P != P_old[l]).nnz == 0
+            A = (P.T @ A @ P).tocsr()
+            Al = s.export(0, l + 1)
+            assert abs(Al - A).max() <= 1e-12 * abs(A).max()
+        o.close()
     s.close()

@@ -11,7 +11,7 @@ the barrier diagonal's spread grows from 1e2 to 1e10 over the systems (Section 4
 Fig. "cond(D)": D's condition number grows exponentially over the IP iterations).
 Training minimises the smoothing loss mean_l ||(I - A_l W_l) r_l||^2 / ||r_l||^2 with
 Adam; forward, backward and update run in the library's CUDA kernels
-(amgf_mlp_train).  The judge of the result is the PCG iteration count on held-out
+(amgf_mlp_train).  The result is measured by the PCG iteration count on held-out
 systems, with theta = 1 (plain AMGF) as the fallback.
 """
 from __future__ import annotations

@@ -1,6 +1,6 @@
 """The minimal interior-point driver (Section 3, Algorithm 1) on the CPU.
 
-The linear solves go through an injected solver backed by the oracle (the driver itself only
+The linear solves go through an injected solver backed by the oracle (the IP loop itself only
 knows the interface); the result is pinned against an independent solution of the same QP:
 the contact pressures y = -lambda >= 0 minimise 1/2 y^T G y + q^T y with G = J K^-1 J^T and
 q = J K^-1 f + g0 (the dual of the QP, a bound-constrained least-squares problem for scipy).

@@ -151,6 +151,34 @@ def contact_jacobian(nx, ny, nz, clamp_bottom=True, clamp_top=True) -> CSR:
     return CSR(m, n, rp, col, val)
 
 
+def contact_jacobian_curved(nx, ny, nz, curvature: float, clamp_bottom=True, clamp_top=True) -> CSR:
+    """Node-to-node contact on an interface with tilted normals: row r constrains
+    n_r . (u_upper - u_lower) for the node pair of row r of contact_jacobian, with the unit
+    normal of the surface z = curvature ((x - 1/2)^2 + (y - 1/2)^2) at the pair's (x, y),
+    n ~ (-2 c (x - 1/2), -2 c (y - 1/2), 1).  Six nonzeros per row (all displacement
+    components of both nodes); curvature = 0 gives the z-only rows of contact_jacobian."""
+    J0 = contact_jacobian(nx, ny, nz, clamp_bottom, clamp_top)
+    xyz = node_xyz(nx, ny, nz, clamp_bottom, clamp_top)
+    m = J0.nrows
+    rp = np.arange(m + 1, dtype=np.int64) * 6
+    col = np.empty(6 * m, dtype=np.int32)
+    val = np.empty(6 * m, dtype=np.float64)
+    for r in range(m):
+        k0, k1 = J0.row_ptr[r], J0.row_ptr[r + 1]
+        cols, vals = J0.col_idx[k0:k1], J0.val[k0:k1]
+        up = int(cols[vals > 0][0]) // 3
+        lo = int(cols[vals < 0][0]) // 3
+        x, y = xyz[up, 0], xyz[up, 1]
+        nrm = np.array([-2.0 * curvature * (x - 0.5), -2.0 * curvature * (y - 0.5), 1.0])
+        nrm /= np.linalg.norm(nrm)
+        a, b = (lo, up) if lo < up else (up, lo)
+        sa = -1.0 if a == lo else 1.0
+        for t, (node, sg) in enumerate(((a, sa), (b, -sa))):
+            col[6 * r + 3 * t:6 * r + 3 * t + 3] = 3 * node + np.arange(3)
+            val[6 * r + 3 * t:6 * r + 3 * t + 3] = sg * nrm
+    return CSR(m, J0.ncols, rp, col, val)
+
+
 def node_xyz(nx, ny, nz, clamp_bottom=True, clamp_top=True) -> np.ndarray:
     lib = _load()
     g = _geom(nx, ny, nz, clamp_bottom, clamp_top)
@@ -198,8 +226,9 @@ def draw_D_b(seed: int, m: int, n: int, d_lo: float, d_hi: float):
 
 
 def make_problem(config: str = "tiny", seed: int = 0, nx=None, ny=None, nz=None,
-                 d_lo=None, d_hi=None) -> Problem:
-    """Generate one seeded two-block problem: K, J, D, b."""
+                 d_lo=None, d_hi=None, curvature: float = 0.0) -> Problem:
+    """Generate one seeded two-block problem: K, J, D, b.  curvature != 0: contact rows with
+    the tilted normals of contact_jacobian_curved instead of z-only rows."""
     c = dict(CONFIGS[config]) if config else {}
     nx = nx if nx is not None else c["nx"]
     ny = ny if ny is not None else c.get("ny", nx)
@@ -207,7 +236,7 @@ def make_problem(config: str = "tiny", seed: int = 0, nx=None, ny=None, nz=None,
     d_lo = d_lo if d_lo is not None else c.get("d_lo", -2.0)
     d_hi = d_hi if d_hi is not None else c.get("d_hi", 4.0)
     K = stiffness(nx, ny, nz)
-    J = contact_jacobian(nx, ny, nz)
+    J = contact_jacobian_curved(nx, ny, nz, curvature) if curvature else contact_jacobian(nx, ny, nz)
     D, b = draw_D_b(seed, J.nrows, K.nrows, d_lo, d_hi)
     return Problem(nx, ny, nz, K.nrows, J.nrows, K, J, D, b,
-                   meta=dict(config=config, seed=seed, d_lo=d_lo, d_hi=d_hi))
+                   meta=dict(config=config, seed=seed, d_lo=d_lo, d_hi=d_hi, curvature=curvature))

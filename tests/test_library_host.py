@@ -189,3 +189,10 @@ def test_update_D_fine_is_galerkin_for_reused_interpolation(dims):
             assert abs(Al - A).max() <= 1e-12 * abs(A).max()
         o.close()
     s.close()
+
+
+def test_host_setup_curved_contact_matches_oracle_bitwise():
+    # contact rows with tilted normals (six nonzeros per row, all components in I_c)
+    p = cg.make_problem(None, nx=10, ny=8, nz=5, d_lo=-2, d_hi=8, seed=3, curvature=1.0)
+    _compare_hierarchy(p)
+    _compare_hierarchy(p, max_coarse=128, p_max=0)

@@ -35,26 +35,29 @@ import time
 import numpy as np
 
 
-def contact_qp(nx: int, ny: int | None = None, nz: int | None = None, load: float = 0.1, curvature: float = 0.2):
+def contact_qp(nx: int, ny: int | None = None, nz: int | None = None, load: float = 0.1, curvature: float = 0.2,
+               tilted: bool = False):
     """Two stacked blocks pressed together: a downward body force on the upper block (the
     lower block's bottom and the upper block's top are clamped) and an initial gap that
     opens quadratically from the interface centre, g0 = curvature ((x - 1/2)^2 + (y - 1/2)^2),
-    so that the contact zone is a disc that grows with the load."""
+    so that the contact zone is a disc that grows with the load.  tilted: the gap is measured
+    along the normal of that curved surface (contact rows n . (u_upper - u_lower), all three
+    components) instead of along z."""
     import contactgen as cg
     ny = nx if ny is None else ny
     nz = max(1, nx // 2) if nz is None else nz
     K = cg.stiffness(nx, ny, nz)
-    J = cg.contact_jacobian(nx, ny, nz)
+    J = cg.contact_jacobian_curved(nx, ny, nz, curvature) if tilted else cg.contact_jacobian(nx, ny, nz)
     xyz = cg.node_xyz(nx, ny, nz)
     nn = xyz.shape[0]
     f = np.zeros(K.nrows)
     h3 = 0.5 / (nx * ny * nz)           # volume per node of one block
     f[3 * np.arange(nn // 2, nn) + 2] = -load * h3  # nodes of the upper block: body force -load
-    Js = J.to_scipy()
-    up = Js.indices[Js.data > 0] // 3   # upper node of each constraint row (one +1 per row)
-    rows = np.repeat(np.arange(J.nrows), np.diff(Js.indptr))
-    up_row = np.empty(J.nrows, dtype=np.int64)
-    up_row[rows[Js.data > 0]] = up
+    Jz = cg.contact_jacobian(nx, ny, nz).to_scipy()  # the node pairs (z-only rows)
+    up = Jz.indices[Jz.data > 0] // 3   # upper node of each constraint row (one +1 per row)
+    rows = np.repeat(np.arange(Jz.shape[0]), np.diff(Jz.indptr))
+    up_row = np.empty(Jz.shape[0], dtype=np.int64)
+    up_row[rows[Jz.data > 0]] = up
     x, y = xyz[up_row, 0], xyz[up_row, 1]
     g0 = curvature * ((x - 0.5) ** 2 + (y - 0.5) ** 2)
     return K, J, f, g0
@@ -195,13 +198,14 @@ if __name__ == "__main__":
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--policy", default="amgf", choices=["amgf", "amg", "switch"])
+    ap.add_argument("--tilted", action="store_true", help="contact along the curved interface's normals")
     ap.add_argument("--switch-spread", type=float, default=1e6)
     ap.add_argument("--lag", type=float, default=None,
                     help="keep the coarse levels while PCG iterations stay within (1 + lag) of the last full setup's")
     ap.add_argument("--save-D", default=None, help="write the IP sequence of D to this .npz")
     ap.add_argument("--json", default=None)
     a = ap.parse_args()
-    K, J, f, g0 = contact_qp(a.nx)
+    K, J, f, g0 = contact_qp(a.nx, tilted=a.tilted)
     u, info = solve(K, J, f, g0, tol=a.tol, precision=a.precision, policy=a.policy, switch_spread=a.switch_spread,
                     verbose=True, record_D=a.save_D is not None, lag=a.lag)
     steps = info["steps"]

@@ -70,3 +70,20 @@ def test_ip_matches_dual_qp_solution(policy):
         assert used == {"amg", "amgf"} and steps[0]["preconditioner"] == "amg"
     else:
         assert used == {policy}
+
+
+def test_tilted_contact_amg_degrades_amgf_flat():
+    # contact measured along the curved interface's normals: along the IP iterations the
+    # PCG iterations of plain AMG grow with D's spread while AMGF's stay flat (Section 6)
+    K, J, f, g0 = ip.contact_qp(8, tilted=True)
+    its = {}
+    for policy in ("amgf", "amg"):
+        u, info = ip.solve(K, J, f, g0, tol=1e-6, policy=policy,
+                           make_solver=lambda D, use_filter: OracleSolver(K, J, D, use_filter))
+        assert info["converged"]
+        its[policy] = [r["pcg_iters"] for r in info["steps"]]
+        u_ref, y_ref = dual_solution(K, J, f, g0)
+        assert np.linalg.norm(u - u_ref) <= 1e-4 * np.linalg.norm(u_ref)
+    a, g = its["amgf"], its["amg"]
+    assert max(a) - min(a) <= 3
+    assert max(g[-3:]) >= 1.5 * g[0] and max(g[-3:]) >= 2.5 * max(a[-3:])

@@ -54,6 +54,13 @@ WORKLOADS = {
 WEIGHTS = os.path.join(ROOT, "paper_2505_18576_gb300", "weights", "smoother_c64.npz")
 
 
+def workload_name(args) -> str:
+    name = f"{args.config}: {WORKLOADS.get(args.config, args.config)}"
+    if args.curvature:
+        name += f"; contact along the normals of a curved interface (curvature {args.curvature:g})"
+    return name
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -121,9 +128,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_inputs(config: str):
+def make_inputs(config: str, curvature: float = 0.0):
     import contactgen as cg
-    p = cg.make_problem(config, seed=0)
+    p = cg.make_problem(config, seed=0, curvature=curvature)
     c = cg.CONFIGS[config]
     rhs = [cg.draw_D_b(s, p.m, p.n, c["d_lo"], c["d_hi"])[1] for s in (0, 1, 2)]
     return p, rhs
@@ -159,7 +166,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    p, rhs = make_inputs(args.config)
+    p, rhs = make_inputs(args.config, args.curvature)
     cores = os.cpu_count()
     o = oracle.Oracle(p.K, p.J, p.D)
     # iteration count of the full solve (untimed, once): scales the per-iteration sample
@@ -177,7 +184,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{args.config}: {WORKLOADS.get(args.config, args.config)}", "rtol": 1e-8,
+            "config": {"workload": workload_name(args), "rtol": 1e-8,
                        "stop": "sqrt(r^T z / r0^T z0)", "parallelism": "host cores (OpenMP row loops)"},
             "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -202,7 +209,7 @@ def run_gpu(args, rank, world, local):
         if dist is not None:
             dist.barrier()
 
-    p, rhs = make_inputs(args.config)
+    p, rhs = make_inputs(args.config, args.curvature)
     t0 = time.perf_counter()
     s = amgf.Solver(p.K, p.J, p.D, use_graph=0 if args.no_graph else 1, precision=args.precision)
     t_setup = time.perf_counter() - t0
@@ -364,7 +371,7 @@ def run_gpu(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32" + ("+bf16" if args.precision >= 2 else ""),
             "data": "synthetic",
-            "config": {"workload": f"{args.config}: {WORKLOADS.get(args.config, args.config)}",
+            "config": {"workload": workload_name(args),
                        "precision": ["fp64", "fp32 V-cycle", "fp32 V-cycle, bf16 fine K",
                                      "fp32 V-cycle, bf16 storage of all V-cycle matrices"][args.precision],
                        "smoother": "l1-Jacobi, learned theta (MLP)" if weights is not None else "l1-Jacobi, theta = 1",
@@ -433,6 +440,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="amgf", choices=["amgf", "reference"])
     ap.add_argument("--config", default="c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--curvature", type=float, default=0.0,
+                    help="contact rows along the normals of a curved interface (0: z-only node-to-node rows)")
     ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations timed for cpu_baseline")
     ap.add_argument("--ref-iters", type=int, default=4, help="oracle PCG iterations per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")

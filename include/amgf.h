@@ -205,6 +205,12 @@ int amgf_matvec(amgf_handle h, const double* x_dev, double* y_dev, void* stream)
  * reduction (filter_algo 0) or block LDL^T sweeps (filter_algo 1). */
 int amgf_filter_solve(amgf_handle h, const double* v_dev, double* w_dev, void* stream);
 
+/* The same solve on the host with the cyclic reduction factor (filter_algo 0), for handles of
+ * amgf_setup_host (a device handle keeps the factor on the device only: AMGF_ERR_INVALID_ARG).
+ * v, w: host arrays of length nc in ascending-DOF order of I_c.  The device solve runs the same
+ * tasks phase by phase, so this checks the factorisation without a GPU. */
+int amgf_filter_solve_host(amgf_handle h, const double* v, double* w);
+
 /* Same result as amgf_filter_solve, for callers that cannot allocate device memory while
  * they run (another allocator owns the device, or a cudaMalloc and the synchronisation it
  * may imply are not allowed in their loop).  The paper has no counterpart: this is a

@@ -20,13 +20,14 @@ from .build import LIB as _LIB_PATH, build as _build
 
 __all__ = ["AmgfError", "Options", "Stats", "Info", "Solver", "load_library", "amgf_options_default",
            "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec", "amgf_filter_solve",
-           "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
+           "amgf_filter_solve_noalloc", "amgf_filter_solve_host", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
            "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED",
            "amgf_setup_bounds", "amgf_update_bounds", "amgf_update_D_fine"]
 
 EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_setup_bounds", "amgf_update_D",
             "amgf_update_bounds", "amgf_update_D_fine", "amgf_apply", "amgf_vcycle", "amgf_matvec",
-            "amgf_filter_solve", "amgf_filter_solve_noalloc", "amgf_pcg_solve", "amgf_pcg_solve_host",
+            "amgf_filter_solve", "amgf_filter_solve_noalloc", "amgf_filter_solve_host", "amgf_pcg_solve",
+            "amgf_pcg_solve_host",
             "amgf_get_info",
             "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
             "amgf_last_error", "amgf_set_mlp", "amgf_mlp_train"]
@@ -99,6 +100,7 @@ def load_library(build_if_missing: bool = True):
         "amgf_matvec": [vp, vp, vp, vp],
         "amgf_filter_solve": [vp, vp, vp, vp],
         "amgf_filter_solve_noalloc": [vp, vp, vp, vp],
+        "amgf_filter_solve_host": [vp, vp, vp],
         "amgf_pcg_solve": [vp, vp, vp, vp, vp],
         "amgf_pcg_solve_host": [vp, vp, vp, vp],
         "amgf_get_info": [vp, vp],
@@ -248,6 +250,14 @@ def amgf_matvec(h, x, y, n: int, stream=None):
 
 def amgf_filter_solve(h, v, w, nc: int, stream=None):
     _check(load_library().amgf_filter_solve(h, _dev_vec(v, nc, "v"), _dev_vec(w, nc, "w"), _stream(stream)))
+
+
+def amgf_filter_solve_host(h, v: np.ndarray) -> np.ndarray:
+    """w = A_w^{-1} v on the host (handles of amgf_setup_host), v in ascending-DOF order of I_c."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    w = np.empty_like(v)
+    _check(load_library().amgf_filter_solve_host(h, _ptr(v), _ptr(w)))
+    return w
 
 
 def amgf_filter_solve_noalloc(h, v, w, nc: int, stream=None):

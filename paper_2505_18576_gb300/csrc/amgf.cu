@@ -1575,6 +1575,14 @@ int amgf_matvec(amgf_handle h, const double* x_dev, double* y_dev, void* stream)
   return join_end(c, stream);
 }
 
+int amgf_filter_solve_host(amgf_handle h, const double* v, double* w) {
+  if (!h || !v || !w) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  if (!h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "the factor of a device handle lives on the device");
+  std::string err;
+  const int st = filter_solve_host(h->c.F, v, w, err);
+  return st ? fail(st, err) : AMGF_OK;
+}
+
 int amgf_filter_solve(amgf_handle h, const double* v_dev, double* w_dev, void* stream) {
   if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
   if (!h || !v_dev || !w_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");

@@ -491,6 +491,53 @@ std::vector<double> transpose_block(int64_t n, const std::vector<double>& a) {
   return t;
 }
 
+// X = B R^{-T} for a lower-triangular R (n x n, row-major): row i of X solves R x = b_i.
+// Forward substitution for 8 rows of B at a time, the inner loops across those 8.
+void solve_rows_lower(int64_t n, const double* R, const double* B, double* X) {
+  constexpr int64_t Q = 8;
+  const int64_t nbat = (n + Q - 1) / Q;
+#pragma omp parallel for schedule(dynamic, 1) if (!omp_in_parallel() && n > 64)
+  for (int64_t bt = 0; bt < nbat; ++bt) {
+    const int64_t r0 = bt * Q, nr = std::min(Q, n - r0);
+    std::vector<double> y(n * Q, 0.0);  // y[i Q + q]: component i of the solution for row r0 + q
+    for (int64_t i = 0; i < n; ++i) {
+      double s[Q];
+      for (int64_t q = 0; q < Q; ++q) s[q] = q < nr ? B[(r0 + q) * n + i] : 0.0;
+      for (int64_t k = 0; k < i; ++k) {
+        const double rik = R[i * n + k];
+        for (int64_t q = 0; q < Q; ++q) s[q] -= rik * y[k * Q + q];
+      }
+      const double d = R[i * n + i];
+      for (int64_t q = 0; q < Q; ++q) y[i * Q + q] = s[q] / d;
+    }
+    for (int64_t q = 0; q < nr; ++q)
+      for (int64_t i = 0; i < n; ++i) X[(r0 + q) * n + i] = y[i * Q + q];
+  }
+}
+
+// X = B R^{-1} for a lower-triangular R: row i of X solves R^T x = b_i (backward substitution,
+// column-oriented so that row k of R is read contiguously), 8 rows of B at a time.
+void solve_rows_upper(int64_t n, const double* R, const double* B, double* X) {
+  constexpr int64_t Q = 8;
+  const int64_t nbat = (n + Q - 1) / Q;
+#pragma omp parallel for schedule(dynamic, 1) if (!omp_in_parallel() && n > 64)
+  for (int64_t bt = 0; bt < nbat; ++bt) {
+    const int64_t r0 = bt * Q, nr = std::min(Q, n - r0);
+    std::vector<double> y(n * Q, 0.0);
+    for (int64_t q = 0; q < nr; ++q)
+      for (int64_t i = 0; i < n; ++i) y[i * Q + q] = B[(r0 + q) * n + i];
+    for (int64_t i = n - 1; i >= 0; --i) {
+      const double d = R[i * n + i];
+      for (int64_t q = 0; q < Q; ++q) y[i * Q + q] /= d;
+      const double* ri = R + i * n;
+      for (int64_t k = 0; k < i; ++k)
+        for (int64_t q = 0; q < Q; ++q) y[k * Q + q] -= ri[k] * y[i * Q + q];
+    }
+    for (int64_t q = 0; q < nr; ++q)
+      for (int64_t i = 0; i < n; ++i) X[(r0 + q) * n + i] = y[i * Q + q];
+  }
+}
+
 // Odd-even block cyclic reduction of the symmetric block-tridiagonal matrix with diagonal
 // blocks A_k and sub-diagonal blocks L_k = A_{k,k-1} (k = 0..N-1).  Eliminating the odd
 // blocks x_k = A_k^{-1} (v_k - L_k x_{k-1} - L_{k+1}^T x_{k+1}) from the even rows leaves a
@@ -519,32 +566,44 @@ int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<dou
   std::vector<std::vector<FilterTask>> fwd, bwd;
   bool spd = true;
   while (N > 1) {
-    std::vector<std::vector<double>> Ainv(N), E(N), Fk(N);
+    std::vector<std::vector<double>> Ainv(N), E(N), Fk(N), R(N);
+    // odd blocks: Cholesky factors R_k (A_k = R_k R_k^T) and the inverses the solve applies
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 1; k < N; k += 2) {
+      std::vector<double> r = A[k];
       std::vector<double> inv;
-      if (!spd_inverse(A[k], nb, inv)) {
+      if (!cholesky(r, nb) || !spd_inverse(A[k], nb, inv)) {
 #pragma omp critical
         spd = false;
       }
+      R[k].swap(r);
       Ainv[k].swap(inv);
     }
     if (!spd) { err = "filter matrix A_w is not SPD"; return AMGF_ERR_NOT_SPD; }
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t k = 0; k < N; k += 2) {
-      if (k >= 1) { E[k].resize(bsz); gemm_nn(nb, L[k].data(), false, Ainv[k - 1].data(), E[k].data(), 1.0, 0.0); }
-      if (k + 1 < N) { Fk[k].resize(bsz); gemm_nn(nb, L[k + 1].data(), true, Ainv[k + 1].data(), Fk[k].data(), 1.0, 0.0); }
-    }
+    // even blocks: the Schur complement A'_k = A_k - W1 W1^T - W2 W2^T with W1 = L_k R_{k-1}^{-T},
+    // W2 = L_{k+1}^T R_{k+1}^{-T} (symmetric updates through the factors, the form that keeps
+    // A' positive definite when the blocks are ill-conditioned), E_k = W1 R_{k-1}^{-1},
+    // F_k = W2 R_{k+1}^{-1}, L'_k = -E_k L_{k-1}
     const int64_t N2 = (N + 1) / 2;
     std::vector<std::vector<double>> A2(N2), L2(N2);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 0; k < N; k += 2) {
-      std::vector<double> a = A[k];
+      std::vector<double> a = A[k], w(bsz), wt;
       if (k >= 1) {
-        const std::vector<double> LT = transpose_block(nb, L[k]);
-        gemm_nn(nb, E[k].data(), false, LT.data(), a.data(), -1.0, 1.0);
+        solve_rows_lower(nb, R[k - 1].data(), L[k].data(), w.data());
+        E[k].resize(bsz);
+        solve_rows_upper(nb, R[k - 1].data(), w.data(), E[k].data());
+        wt = transpose_block(nb, w);
+        gemm_nn(nb, w.data(), false, wt.data(), a.data(), -1.0, 1.0);
       }
-      if (k + 1 < N) gemm_nn(nb, Fk[k].data(), false, L[k + 1].data(), a.data(), -1.0, 1.0);
+      if (k + 1 < N) {
+        const std::vector<double> LT = transpose_block(nb, L[k + 1]);
+        solve_rows_lower(nb, R[k + 1].data(), LT.data(), w.data());
+        Fk[k].resize(bsz);
+        solve_rows_upper(nb, R[k + 1].data(), w.data(), Fk[k].data());
+        wt = transpose_block(nb, w);
+        gemm_nn(nb, w.data(), false, wt.data(), a.data(), -1.0, 1.0);
+      }
       for (int64_t r = 0; r < nb; ++r)
         for (int64_t c = r + 1; c < nb; ++c) {
           const double sym = 0.5 * (a[r * nb + c] + a[c * nb + r]);
@@ -1016,6 +1075,40 @@ void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, c
     for (int64_t i = 0; i < nl; ++i)
       if (H.cf[l][i]) { d[c] = d[i]; flag[c] = flag[i]; ++c; }
   }
+}
+
+int filter_solve_host(const Filter& F, const double* v_ic, double* w_ic, std::string& err) {
+  if (F.nc == 0) { err = "empty contact set"; return AMGF_ERR_INVALID_ARG; }
+  if (F.algo != 0 || F.M.empty()) { err = "no cyclic reduction factor on the host"; return AMGF_ERR_INVALID_ARG; }
+  const int64_t nb = F.nb, tot = nb * F.nblk;
+  // factor position p -> place of DOF gidx[p] in I_c (ascending)
+  std::vector<int64_t> place(F.nc);
+  for (int64_t p = 0; p < F.nc; ++p)
+    place[p] = std::lower_bound(F.ic.begin(), F.ic.end(), F.gidx[p]) - F.ic.begin();
+  std::vector<double> v(tot, 0.0), x(tot, 0.0), in0(nb), in1(nb);
+  for (int64_t p = 0; p < F.nc; ++p) v[p] = v_ic[place[p]];
+  const int nphase = (int)F.phase_off.size() - 1;
+  for (int q = 0; q < nphase; ++q) {
+    for (int64_t t = F.phase_off[q]; t < F.phase_off[q + 1]; ++t) {
+      const FilterTask& T = F.tasks[t];
+      const std::vector<double>& src = T.kind == 2 ? x : v;
+      if (T.in0 >= 0) std::copy(src.begin() + (int64_t)T.in0 * nb, src.begin() + (int64_t)(T.in0 + 1) * nb, in0.begin());
+      if (T.in1 >= 0) std::copy(src.begin() + (int64_t)T.in1 * nb, src.begin() + (int64_t)(T.in1 + 1) * nb, in1.begin());
+      for (int64_t row = 0; row < nb; ++row) {
+        double s = 0.0;
+        if (T.m0 >= 0 && T.in0 >= 0)
+          for (int64_t c = 0; c < nb; ++c) s += F.M[(T.m0 * nb + row) * nb + c] * in0[c];
+        if (T.m1 >= 0 && T.in1 >= 0)
+          for (int64_t c = 0; c < nb; ++c) s += F.M[(T.m1 * nb + row) * nb + c] * in1[c];
+        const int64_t p = (int64_t)T.out * nb + row;
+        if (T.kind == 0) x[p] = s;
+        else if (T.kind == 1) v[p] = v[p] - s;
+        else x[p] = x[p] - s;
+      }
+    }
+  }
+  for (int64_t p = 0; p < F.nc; ++p) w_ic[place[p]] = x[p];
+  return AMGF_OK;
 }
 
 int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter& F, std::string& err) {

@@ -128,5 +128,9 @@ void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, c
 // I_c, A_w = A[I_c, I_c], reverse Cuthill-McKee order, and the exact solver of the
 // block-tridiagonal A_w: block cyclic reduction (o.filter_algo 0) or block LDL^T (1).
 int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter& F, std::string& err);
+// w = A_w^{-1} v on the host with the cyclic reduction factor (the task semantics of the
+// device solve, phase by phase); v, w of length nc in ascending-DOF order of I_c.
+int filter_solve_host(const Filter& F, const double* v_ic, double* w_ic, std::string& err);
+
 
 }  // namespace amgf

@@ -196,3 +196,28 @@ def test_host_setup_curved_contact_matches_oracle_bitwise():
     p = cg.make_problem(None, nx=10, ny=8, nz=5, d_lo=-2, d_hi=8, seed=3, curvature=1.0)
     _compare_hierarchy(p)
     _compare_hierarchy(p, max_coarse=128, p_max=0)
+
+
+@pytest.mark.parametrize("case", ["z8", "z16", "curved16_1e6", "curved16_1e10"])
+def test_host_filter_solve_matches_oracle(case):
+    # the cyclic reduction factor applied on the host (the device solve's task semantics)
+    # against the oracle's banded Cholesky: backward error and the kappa(A_w) forward bound.
+    # With tilted contact normals and D up to 1e10, kappa(A_w) ~ 1e13: the Schur complements
+    # are formed through the blocks' Cholesky factors, which keeps them positive definite
+    dims, curv, dh = {"z8": ((8, 8, 4), 0.0, 8.0), "z16": ((16, 12, 7), 0.0, 8.0),
+                      "curved16_1e6": ((16, 16, 8), 1.0, 6.0), "curved16_1e10": ((16, 16, 8), 1.0, 10.0)}[case]
+    p = cg.make_problem(None, nx=dims[0], ny=dims[1], nz=dims[2], d_lo=-2, d_hi=dh, seed=2, curvature=curv)
+    s = amgf.Solver(p.K, p.J, p.D, host_only=True)
+    o = oracle.Oracle(p.K, p.J, p.D)
+    Ic = o.Ic()
+    Aw = o.S()[Ic][:, Ic].toarray()
+    ev = np.linalg.eigvalsh(Aw)
+    v = np.random.default_rng(3).standard_normal(len(Ic))
+    w = amgf.amgf_filter_solve_host(s.h, v)
+    wo = o.filter_solve(v)
+    eps = np.finfo(np.float64).eps
+    back = np.linalg.norm(Aw @ w - v) / (np.linalg.norm(Aw, 2) * np.linalg.norm(w))
+    assert back <= 64 * eps
+    assert np.linalg.norm(w - wo) <= max(1e-12, 16 * eps * ev[-1] / ev[0]) * np.linalg.norm(wo)
+    s.close()
+    o.close()

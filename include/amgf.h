@@ -205,7 +205,7 @@ int amgf_matvec(amgf_handle h, const double* x_dev, double* y_dev, void* stream)
  * reduction (filter_algo 0) or block LDL^T sweeps (filter_algo 1). */
 int amgf_filter_solve(amgf_handle h, const double* v_dev, double* w_dev, void* stream);
 
-/* The same solve on the host with the cyclic reduction factor (filter_algo 0), for handles of
+/* The same solve on the host with the filter's factor (either filter_algo), for handles of
  * amgf_setup_host (a device handle keeps the factor on the device only: AMGF_ERR_INVALID_ARG).
  * v, w: host arrays of length nc in ascending-DOF order of I_c.  The device solve runs the same
  * tasks phase by phase, so this checks the factorisation without a GPU. */

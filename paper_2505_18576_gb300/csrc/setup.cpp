@@ -1079,7 +1079,6 @@ void smoother_features(const Hierarchy& H, const amgf_csr* J, const double* D, c
 
 int filter_solve_host(const Filter& F, const double* v_ic, double* w_ic, std::string& err) {
   if (F.nc == 0) { err = "empty contact set"; return AMGF_ERR_INVALID_ARG; }
-  if (F.algo != 0 || F.M.empty()) { err = "no cyclic reduction factor on the host"; return AMGF_ERR_INVALID_ARG; }
   const int64_t nb = F.nb, tot = nb * F.nblk;
   // factor position p -> place of DOF gidx[p] in I_c (ascending)
   std::vector<int64_t> place(F.nc);
@@ -1087,6 +1086,31 @@ int filter_solve_host(const Filter& F, const double* v_ic, double* w_ic, std::st
     place[p] = std::lower_bound(F.ic.begin(), F.ic.end(), F.gidx[p]) - F.ic.begin();
   std::vector<double> v(tot, 0.0), x(tot, 0.0), in0(nb), in1(nb);
   for (int64_t p = 0; p < F.nc; ++p) v[p] = v_ic[place[p]];
+  if (F.algo == 1) {  // block LDL^T: y_i = v_i - G_i y_{i-1}; z_i = D_i^{-1} y_i; w_i = z_i - G_{i+1}^T w_{i+1}
+    if (F.G.empty()) { err = "no factor on the host"; return AMGF_ERR_INVALID_ARG; }
+    const int64_t bsz = nb * nb;
+    for (int64_t i = 1; i < F.nblk; ++i)
+      for (int64_t r = 0; r < nb; ++r) {
+        double acc = 0.0;
+        for (int64_t c = 0; c < nb; ++c) acc += F.G[i * bsz + r * nb + c] * v[(i - 1) * nb + c];
+        v[i * nb + r] -= acc;
+      }
+    for (int64_t i = 0; i < F.nblk; ++i)
+      for (int64_t r = 0; r < nb; ++r) {
+        double acc = 0.0;
+        for (int64_t c = 0; c < nb; ++c) acc += F.Dinv[i * bsz + r * nb + c] * v[i * nb + c];
+        x[i * nb + r] = acc;
+      }
+    for (int64_t i = F.nblk - 2; i >= 0; --i)
+      for (int64_t r = 0; r < nb; ++r) {
+        double acc = 0.0;
+        for (int64_t c = 0; c < nb; ++c) acc += F.GT[(i + 1) * bsz + r * nb + c] * x[(i + 1) * nb + c];
+        x[i * nb + r] -= acc;
+      }
+    for (int64_t p = 0; p < F.nc; ++p) w_ic[place[p]] = x[p];
+    return AMGF_OK;
+  }
+  if (F.M.empty()) { err = "no cyclic reduction factor on the host"; return AMGF_ERR_INVALID_ARG; }
   const int nphase = (int)F.phase_off.size() - 1;
   for (int q = 0; q < nphase; ++q) {
     for (int64_t t = F.phase_off[q]; t < F.phase_off[q + 1]; ++t) {
@@ -1243,15 +1267,19 @@ int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter
   F.Dinv.assign(nblk * bsz, 0.0);
   F.G.assign(nblk * bsz, 0.0);
   F.GT.assign(nblk * bsz, 0.0);
-  std::vector<double> Dcur(Ad.begin(), Ad.begin() + bsz), tmp(bsz), AsT(bsz);
+  std::vector<double> Dcur(Ad.begin(), Ad.begin() + bsz), Rprev, W(bsz), WT(bsz);
   for (int64_t i = 0; i < nblk; ++i) {
     if (i > 0) {
+      // D_i = A_i - W W^T with W = A_{i,i-1} R_{i-1}^{-T} (R_{i-1} the Cholesky factor of
+      // D_{i-1}) and G_i = W R_{i-1}^{-1}: the update through the factor keeps D_i positive
+      // definite when the pivots are ill-conditioned
       Dcur.assign(Ad.begin() + i * bsz, Ad.begin() + (i + 1) * bsz);
       double* Gi = F.G.data() + i * bsz;
-      gemm(nb, As.data() + i * bsz, F.Dinv.data() + (i - 1) * bsz, Gi, 1.0, 0.0);
+      solve_rows_lower(nb, Rprev.data(), As.data() + i * bsz, W.data());
+      solve_rows_upper(nb, Rprev.data(), W.data(), Gi);
       for (int64_t r = 0; r < nb; ++r)
-        for (int64_t c = 0; c < nb; ++c) AsT[r * nb + c] = As[i * bsz + c * nb + r];
-      gemm(nb, Gi, AsT.data(), Dcur.data(), -1.0, 1.0);
+        for (int64_t c = 0; c < nb; ++c) WT[r * nb + c] = W[c * nb + r];
+      gemm(nb, W.data(), WT.data(), Dcur.data(), -1.0, 1.0);
       for (int64_t r = 0; r < nb; ++r)
         for (int64_t c = r + 1; c < nb; ++c) {
           const double s = 0.5 * (Dcur[r * nb + c] + Dcur[c * nb + r]);
@@ -1261,7 +1289,11 @@ int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter
         for (int64_t c = 0; c < nb; ++c) F.GT[i * bsz + r * nb + c] = Gi[c * nb + r];
     }
     std::vector<double> inv;
-    if (!spd_inverse(Dcur, nb, inv)) { err = "filter matrix A_w is not SPD"; return AMGF_ERR_NOT_SPD; }
+    Rprev = Dcur;
+    if (!cholesky(Rprev, nb) || !spd_inverse(Dcur, nb, inv)) {
+      err = "filter matrix A_w is not SPD";
+      return AMGF_ERR_NOT_SPD;
+    }
     std::copy(inv.begin(), inv.end(), F.Dinv.begin() + i * bsz);
   }
   }

@@ -198,8 +198,9 @@ def test_host_setup_curved_contact_matches_oracle_bitwise():
     _compare_hierarchy(p, max_coarse=128, p_max=0)
 
 
+@pytest.mark.parametrize("algo", [0, 1])
 @pytest.mark.parametrize("case", ["z8", "z16", "curved16_1e6", "curved16_1e10"])
-def test_host_filter_solve_matches_oracle(case):
+def test_host_filter_solve_matches_oracle(case, algo):
     # the cyclic reduction factor applied on the host (the device solve's task semantics)
     # against the oracle's banded Cholesky: backward error and the kappa(A_w) forward bound.
     # With tilted contact normals and D up to 1e10, kappa(A_w) ~ 1e13: the Schur complements
@@ -207,7 +208,7 @@ def test_host_filter_solve_matches_oracle(case):
     dims, curv, dh = {"z8": ((8, 8, 4), 0.0, 8.0), "z16": ((16, 12, 7), 0.0, 8.0),
                       "curved16_1e6": ((16, 16, 8), 1.0, 6.0), "curved16_1e10": ((16, 16, 8), 1.0, 10.0)}[case]
     p = cg.make_problem(None, nx=dims[0], ny=dims[1], nz=dims[2], d_lo=-2, d_hi=dh, seed=2, curvature=curv)
-    s = amgf.Solver(p.K, p.J, p.D, host_only=True)
+    s = amgf.Solver(p.K, p.J, p.D, host_only=True, filter_algo=algo)
     o = oracle.Oracle(p.K, p.J, p.D)
     Ic = o.Ic()
     Aw = o.S()[Ic][:, Ic].toarray()

@@ -83,6 +83,10 @@ def _load():
         getattr(lib, f).restype = i32
     lib.orc_set_mlp.argtypes = [vp, vp, i64]
     lib.orc_set_mlp.restype = i32
+    lib.orc_mlp_loss.argtypes = [vp, vp, vp]
+    lib.orc_mlp_loss.restype = i32
+    lib.orc_set_threads.argtypes = [i32]
+    lib.orc_set_threads.restype = i32
     _lib = lib
     return lib
 
@@ -237,6 +241,16 @@ class Oracle:
         if st:
             raise OracleError(st, "set_mlp")
 
+    def mlp_loss(self, r_all):
+        """Mean over the smoothed levels of ||(I - A_l W_l) r_l||^2 / ||r_l||^2 with the active
+        weights; r_all holds the per-level vectors back to back (every level but the coarsest)."""
+        r = np.ascontiguousarray(r_all, np.float64)
+        out = ctypes.c_double()
+        st = self._lib.orc_mlp_loss(self._h, _p(r), ctypes.byref(out))
+        if st:
+            raise OracleError(st, "mlp_loss")
+        return out.value
+
     def theta(self, l):
         out = np.empty(self.A(l).shape[0])
         if self._lib.orc_get_theta(self._h, l, _p(out)):
@@ -246,3 +260,8 @@ class Oracle:
     def func(self, l):
         out = np.empty(self.A(l).shape[0], np.int32)
         self._lib.orc_get_func(self._h, l, _p(out)); return out
+
+
+def set_threads(k: int) -> int:
+    """Threads of the oracle's parallel loops (k <= 0 leaves them); returns the previous count."""
+    return int(_load().orc_set_threads(int(k)))

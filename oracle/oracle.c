@@ -50,6 +50,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1076,6 +1079,49 @@ int orc_set_mlp(orc_t* h, const double* w, int64_t nw) {
   }
   free(dl); free(cl);
   return ORC_OK;
+}
+
+/* Training objective of the learned smoother (not in the paper): the error reduction of one
+ * damped l1-Jacobi step on given vectors, averaged over the smoothed levels,
+ *   L = (1 / (nlev - 1)) sum_l ||(I - A_l W_l) r_l||^2 / ||r_l||^2,   W_l = diag(theta_l / l1_l),
+ * theta from the active weights (orc_set_mlp), theta = 1 without them.  r_all holds r_0, r_1,
+ * ..., r_{nlev-2} back to back (n_l values each). */
+int orc_mlp_loss(orc_t* h, const double* r_all, double* loss) {
+  orc_amg* g = &h->amg;
+  if (g->nlev < 2) return ORC_INVALID;
+  double sum = 0.0;
+  const double* r = r_all;
+  for (int l = 0; l + 1 < g->nlev; ++l) {
+    const ocsr* A = &g->A[l];
+    const int64_t n = A->nrows;
+    double* x = xmalloc(n * sizeof(double));
+    double* e = xmalloc(n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+      const double th = g->theta[l] ? g->theta[l][i] : 1.0;
+      x[i] = (th / g->l1[l][i]) * r[i];
+    }
+    csr_resid(A, r, x, e); /* e = r - A W r */
+    double ee = 0.0, rr = 0.0;
+    for (int64_t i = 0; i < n; ++i) { ee += e[i] * e[i]; rr += r[i] * r[i]; }
+    sum += ee / rr;
+    free(x); free(e);
+    r += n;
+  }
+  *loss = sum / (double)(g->nlev - 1);
+  return ORC_OK;
+}
+
+/* Threads of the parallel loops (A x and residuals); returns the previous setting.  Used by the
+ * benchmark to time the oracle single-threaded and on all cores. */
+int orc_set_threads(int k) {
+#ifdef _OPENMP
+  const int prev = omp_get_max_threads();
+  if (k > 0) omp_set_num_threads(k);
+  return prev;
+#else
+  (void)k;
+  return 1;
+#endif
 }
 
 int orc_get_theta(orc_t* h, int l, double* out) {

@@ -102,3 +102,77 @@ def test_theta_inherited_contact_features(tiny):
     Ic = o.Ic()
     assert np.all(f0[Ic, 3] == 1.0) and f0[:, 3].sum() == len(Ic)
     assert np.all(f0[Ic, 4] > 0)
+
+
+# ---------------------------------------------------------------- training objective
+class _Csr:
+    def __init__(self, M):
+        M = M.tocsr()
+        M.sort_indices()
+        self.row_ptr = M.indptr.astype(np.int64)
+        self.col_idx = M.indices.astype(np.int32)
+        self.val = M.data.astype(np.float64)
+        self.nrows, self.ncols = M.shape
+
+
+def _periodic_laplacian(N, s):
+    import scipy.sparse as sp
+    e = np.ones(N)
+    A = sp.diags([-e[:-1], (2 + s) * e, -e[:-1]], [-1, 0, 1], format="lil")
+    A[0, N - 1] = -1.0
+    A[N - 1, 0] = -1.0
+    return A.tocsr()
+
+
+def _constant_theta_weights(beta):
+    w = np.zeros(MLP_NW)
+    w[1312] = beta
+    return w
+
+
+@pytest.mark.parametrize("k,beta", [(1, 0.0), (5, 1.5), (16, -2.0)])
+def test_training_loss_closed_form_on_a_fourier_mode(k, beta):
+    # A = circulant tridiag(-1, 2 + s, -1): every row has l1 = 4 + s, and r_i = cos(2 pi k i / N)
+    # is an eigenvector with lambda_k = 2 + s - 2 cos(2 pi k / N).  With weights that make theta
+    # constant (all but the output bias zero: theta = 0.3 + 0.9 sigmoid(beta)), one damped
+    # l1-Jacobi step maps r to (1 - theta lambda_k / (4 + s)) r, so the objective of the one
+    # smoothed level is (1 - theta lambda_k / (4 + s))^2; its derivative in beta follows.
+    N, s = 64, 0.5
+    A = _periodic_laplacian(N, s)
+    o = oracle.Oracle(_Csr(A), num_functions=1, max_coarse=N // 2 + 10)
+    assert o.nlev == 2 and np.allclose(o.l1(0), 4 + s)
+    r = np.cos(2 * np.pi * k * np.arange(N) / N)
+    lam = 2 + s - 2 * np.cos(2 * np.pi * k / N)
+    q = lam / (4 + s)
+    sig = 1 / (1 + np.exp(-beta))
+    theta = 0.3 + 0.9 * sig
+    o.set_mlp(_constant_theta_weights(beta))
+    assert np.isclose(o.mlp_loss(r), (1 - theta * q) ** 2, rtol=1e-12, atol=1e-15)
+    o.set_mlp(None)
+    assert np.isclose(o.mlp_loss(r), (1 - q) ** 2, rtol=1e-12, atol=1e-15)
+    # central difference of the oracle's loss in beta against the closed-form derivative
+    h = 1e-5
+    o.set_mlp(_constant_theta_weights(beta + h))
+    lp = o.mlp_loss(r)
+    o.set_mlp(_constant_theta_weights(beta - h))
+    lm = o.mlp_loss(r)
+    dref = 2 * (1 - theta * q) * (-q) * 0.9 * sig * (1 - sig)
+    assert abs((lp - lm) / (2 * h) - dref) <= 1e-8 * max(1.0, abs(dref))
+
+
+def test_training_loss_averages_levels(tiny):
+    # the objective is a mean of per-level ratios ||e_l||^2 / ||r_l||^2: invariant under scaling
+    # all vectors, or one level's vector alone, and equal for theta = 1 with or without a model
+    # whose output is exactly 1
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, max_coarse=128)
+    ns = [o.A(l).shape[0] for l in range(o.nlev - 1)]
+    assert len(ns) >= 2
+    r = np.random.default_rng(0).uniform(-1, 1, sum(ns))
+    base = o.mlp_loss(r)
+    assert np.isclose(o.mlp_loss(3.0 * r), base, rtol=1e-13)
+    o.set_mlp(unit_theta_weights())
+    assert np.isclose(o.mlp_loss(r), base, rtol=1e-13)
+    r2 = r.copy()
+    r2[:ns[0]] *= -7.0
+    assert np.isclose(o.mlp_loss(r2), base, rtol=1e-13)
+    assert 0.0 < base < 1.0

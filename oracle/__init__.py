@@ -46,7 +46,7 @@ class Opts(ctypes.Structure):
                 ("nu", ctypes.c_int), ("filter", ctypes.c_int),
                 ("contact_components", ctypes.c_int), ("build_amg", ctypes.c_int),
                 ("interp", ctypes.c_int), ("p_max", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("cheby_lower", ctypes.c_double)]
+                ("cheby_lower", ctypes.c_double), ("hier_from_K", ctypes.c_int)]
 
 
 def _load():

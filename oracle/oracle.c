@@ -87,6 +87,9 @@ typedef struct {
   int p_max;             /* interpolation truncation: at most p_max weights per F row (4; 0: none) */
   int smoother;          /* 0: l1-Jacobi (nu sweeps); 1: Chebyshev of degree nu in W A */
   double cheby_lower;    /* Chebyshev: the polynomial damps eigenvalues of W A in [cheby_lower, 1] */
+  int hier_from_K;       /* 1: strength, coarsening and interpolation from the stiffness hierarchy
+                            K_{l+1} = R_l K_l P_l, operators A_l = K_l + J_l^T D J_l with
+                            J_{l+1} = J_l P_l (a variant; the paper builds B := AMG(A)) */
 } orc_opts;
 
 typedef struct {
@@ -523,9 +526,32 @@ static void dense_chol_solve(const double* L, int64_t n, const double* b, double
   }
 }
 
-static int amg_setup(orc_t* h) {
+static void csr_copy(const ocsr* a, ocsr* b) {
+  const int64_t nnz = a->rp[a->nrows];
+  b->nrows = a->nrows; b->ncols = a->ncols;
+  b->rp = xmalloc((a->nrows + 1) * sizeof(int64_t));
+  b->ci = xmalloc((nnz ? nnz : 1) * sizeof(int32_t));
+  b->v = xmalloc((nnz ? nnz : 1) * sizeof(double));
+  memcpy(b->rp, a->rp, (a->nrows + 1) * sizeof(int64_t));
+  memcpy(b->ci, a->ci, nnz * sizeof(int32_t));
+  memcpy(b->v, a->v, nnz * sizeof(double));
+}
+
+/* K, J, D: the inputs, used by the K-based variant (o->hier_from_K) only:
+ *   strength, coarsening and interpolation of level l from K_l (K_0 = K, K_{l+1} = R_l K_l P_l),
+ *   J_{l+1} = J_l P_l, and the level operator A_{l+1} = K_{l+1} + J_{l+1}^T D J_{l+1}
+ *   (the same matrix as R_l A_l P_l in exact arithmetic). */
+static int amg_setup(orc_t* h, const ocsr* K, const ocsr* J, const double* D) {
   orc_amg* g = &h->amg;
   const orc_opts* o = &h->o;
+  const int fromK = o->hier_from_K && K;
+  ocsr Kl, Jl;
+  memset(&Kl, 0, sizeof Kl);
+  memset(&Jl, 0, sizeof Jl);
+  if (fromK) {
+    csr_copy(K, &Kl);
+    if (J && J->nrows > 0) csr_copy(J, &Jl);
+  }
   /* level 0 operator is a copy of S */
   ocsr* A0 = &g->A[0];
   A0->nrows = h->S.nrows; A0->ncols = h->S.ncols;
@@ -549,12 +575,13 @@ static int amg_setup(orc_t* h) {
       g->l1[l][i] = s;
     }
     if (n <= o->max_coarse || l + 1 >= o->max_levels || l + 1 >= 32) break;
+    const ocsr* H = fromK ? &Kl : A; /* the matrix the hierarchy is built from */
     ocsr Sg;
-    strength(A, g->func[l], o->strength_theta, &Sg);
+    strength(H, g->func[l], o->strength_theta, &Sg);
     g->cf[l] = xmalloc(n);
     rs_coarsen(&Sg, g->cf[l]);
     int64_t nc = 0;
-    build_interp(A, &Sg, g->func[l], g->cf[l], o->interp, o->p_max, &g->P[l], &nc);
+    build_interp(H, &Sg, g->func[l], g->cf[l], o->interp, o->p_max, &g->P[l], &nc);
     csr_free(&Sg);
     if (nc == 0 || nc == n) { /* coarsening stalled: this level is the coarsest */
       csr_free(&g->P[l]); free(g->cf[l]); g->cf[l] = NULL;
@@ -562,15 +589,34 @@ static int amg_setup(orc_t* h) {
     }
     csr_transpose(&g->P[l], &g->R[l]);
     ocsr AP;
-    csr_matmul(A, &g->P[l], &AP);
-    csr_matmul(&g->R[l], &AP, &g->A[l + 1]);
-    csr_free(&AP);
+    if (fromK) {
+      /* K_{l+1} = R K_l P, J_{l+1} = J_l P, A_{l+1} = K_{l+1} + J_{l+1}^T D J_{l+1} */
+      ocsr Kc, JP;
+      csr_matmul(&Kl, &g->P[l], &AP);
+      csr_matmul(&g->R[l], &AP, &Kc);
+      csr_free(&AP);
+      csr_free(&Kl);
+      Kl = Kc;
+      if (Jl.nrows > 0) {
+        csr_matmul(&Jl, &g->P[l], &JP);
+        csr_free(&Jl);
+        Jl = JP;
+        assemble_S(&Kl, &Jl, D, &g->A[l + 1]);
+      } else {
+        csr_copy(&Kl, &g->A[l + 1]);
+      }
+    } else {
+      csr_matmul(A, &g->P[l], &AP);
+      csr_matmul(&g->R[l], &AP, &g->A[l + 1]);
+      csr_free(&AP);
+    }
     g->func[l + 1] = xmalloc(nc * sizeof(int32_t));
     for (int64_t i = 0, c = 0; i < n; ++i)
       if (g->cf[l][i]) g->func[l + 1][c++] = g->func[l][i];
     l++;
   }
   g->nlev = l + 1;
+  if (fromK) { csr_free(&Kl); csr_free(&Jl); }
   /* coarsest: dense Cholesky */
   ocsr* AL = &g->A[l];
   int64_t nL = AL->nrows;
@@ -819,6 +865,7 @@ void orc_opts_default(orc_opts* o) {
   o->p_max = 4;
   o->smoother = 0;
   o->cheby_lower = 0.3;
+  o->hier_from_K = 0;
 }
 
 const char* orc_error(orc_t* h) { return h ? h->err : "null handle"; }
@@ -894,7 +941,8 @@ int orc_create_bounds(int64_t n,
     *out = h;
     return ORC_OK;
   }
-  int st = amg_setup(h);
+  if (h->o.hier_from_K && E) { orc_free(h); return ORC_INVALID; } /* variant without bound terms */
+  int st = amg_setup(h, &K, &J, D);
   if (st != ORC_OK) { *out = h; return st; }
   if (h->o.filter) {
     if (m > 0 || h->o.contact_components == 2) contact_set(h, &J);

@@ -113,6 +113,11 @@ typedef struct {
   int64_t kernel_launches;/* this library's kernels executed by the solve */
   int mlp_fallback;       /* 1: the learned weights missed the stop test and the solve was redone
                              with theta = 1 (the plain l1-Jacobi smoother) */
+  double rel_res_l2;      /* true relative residual ||b - A x||_2 / ||b||_2 of the returned x, from
+                             one FP64 A x after the solve (not part of t_solve_s); 0 when b = 0.
+                             With barrier entries up to D_max it stalls near u D_max |x| / |b|
+                             while the preconditioned norm of the stop test keeps falling. */
+  double t_setup_s;       /* host setup and upload time of the handle (amgf_info.t_setup_s) */
 } amgf_stats;
 
 typedef struct {
@@ -193,6 +198,16 @@ int amgf_update_bounds(amgf_handle h, const double* D, const double* d_lower, co
  * With filter = 0: z = B r.  Both vectors have length n.  r_dev and z_dev must not alias. */
 int amgf_apply(amgf_handle h, const double* r_dev, double* z_dev, void* stream);
 
+/* amgf_apply with copies of its intermediate vectors (tests; Definition "AMGF" in the product
+ * form of Section 5.1): y1 = B r, r1 = r - A y1, w = A_w^{-1} P^T r1 (length nc, ascending-DOF
+ * order of I_c) and r2 = r1 - A P w, each written to the caller's device buffer when its pointer
+ * is not NULL; z_dev receives z = y1 + P w + B r2 exactly as amgf_apply computes it.  The copies
+ * let a test check each step on the library's own vectors, e.g. that P^T r2 = P^T r1 - A_w w
+ * vanishes to rounding whatever kappa(A_w) is.  w and r2 need options.filter = 1 and a nonempty
+ * I_c (AMGF_ERR_INVALID_ARG otherwise); with filter = 0 (M = B) only y1 = z is written. */
+int amgf_apply_stages(amgf_handle h, const double* r_dev, double* z_dev, double* y1_dev, double* r1_dev,
+                      double* w_dev, double* r2_dev, void* stream);
+
 /* x_dev = B r_dev, one V-cycle from a zero start (the B of Section 5.1). */
 int amgf_vcycle(amgf_handle h, const double* r_dev, double* x_dev, void* stream);
 
@@ -257,6 +272,15 @@ int amgf_set_mlp(amgf_handle h, const float* weights, int64_t nw);
 int amgf_mlp_train(amgf_handle h, float* params, float* adam_m, float* adam_v, int64_t* adam_step,
                    int iters, float lr, uint64_t seed, float* loss);
 
+/* The training objective of amgf_mlp_train and its gradient for given weights and given
+ * vectors r_l (tests: the same kernels as one training step, without the Adam update).
+ * params: 1313 floats (layout of amgf_set_mlp); r_all: host array holding r_0, r_1, ...,
+ * r_{L-2} back to back (level_rows[l] doubles each, every level but the coarsest);
+ * *loss = mean_l ||(I - A_l W_l) r_l||^2 / ||r_l||^2 (may be NULL); grad: 1313 floats,
+ * d loss / d params.  Needs an FP64 handle with >= 2 levels.  The active smoother weights are
+ * left unchanged. */
+int amgf_mlp_grad(amgf_handle h, const float* params, const double* r_all, float* grad, double* loss);
+
 /* Hierarchy and sizes. */
 int amgf_get_info(amgf_handle h, amgf_info* info);
 
@@ -271,7 +295,8 @@ int amgf_export_contact_set(amgf_handle h, int64_t* ic);
 /* Time `reps` back-to-back launches of one kernel of the solve phase on `stream`
  * with CUDA events, after `warmup` untimed launches.  which: 0 = fine-level
  * A x (SpMV of level 0), 1 = fine-level FP64 post-smoother, 2 = fine-level post-smoother
- * of the FP32 V-cycle (mixed-precision handles only).  *ms = average per launch;
+ * of the FP32 V-cycle (mixed-precision handles only), 3 = level-1 post-smoother in the
+ * V-cycle's precision (hierarchies of >= 3 levels).  *ms = average per launch;
  * *bytes = algorithmic bytes one launch moves (values + indices + vectors). */
 int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* stream,
                      double* ms, double* bytes);

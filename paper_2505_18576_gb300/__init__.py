@@ -22,7 +22,7 @@ __all__ = ["AmgfError", "Options", "Stats", "Info", "Solver", "load_library", "a
            "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec", "amgf_filter_solve",
            "amgf_filter_solve_noalloc", "amgf_filter_solve_host", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
            "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED",
-           "amgf_setup_bounds", "amgf_update_bounds", "amgf_update_D_fine"]
+           "amgf_setup_bounds", "amgf_update_bounds", "amgf_update_D_fine", "amgf_apply_stages", "amgf_mlp_grad"]
 
 EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_setup_bounds", "amgf_update_D",
             "amgf_update_bounds", "amgf_update_D_fine", "amgf_apply", "amgf_vcycle", "amgf_matvec",
@@ -30,7 +30,7 @@ EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_setup
             "amgf_pcg_solve_host",
             "amgf_get_info",
             "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
-            "amgf_last_error", "amgf_set_mlp", "amgf_mlp_train"]
+            "amgf_last_error", "amgf_set_mlp", "amgf_mlp_train", "amgf_apply_stages", "amgf_mlp_grad"]
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "NOT_SPD", 4: "BREAKDOWN", 5: "NOT_CONVERGED",
           6: "CUDA", 7: "OOM"}
@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("rel_res_precond", ctypes.c_double), ("rz0", ctypes.c_double),
                 ("t_solve_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("mlp_fallback", ctypes.c_int)]
+                ("mlp_fallback", ctypes.c_int), ("rel_res_l2", ctypes.c_double), ("t_setup_s", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -96,6 +96,7 @@ def load_library(build_if_missing: bool = True):
         "amgf_update_bounds": [vp, vp, vp, vp],
         "amgf_update_D_fine": [vp, vp],
         "amgf_apply": [vp, vp, vp, vp],
+        "amgf_apply_stages": [vp, vp, vp, vp, vp, vp, vp, vp],
         "amgf_vcycle": [vp, vp, vp, vp],
         "amgf_matvec": [vp, vp, vp, vp],
         "amgf_filter_solve": [vp, vp, vp, vp],
@@ -110,6 +111,7 @@ def load_library(build_if_missing: bool = True):
         "amgf_destroy": [vp],
         "amgf_set_mlp": [vp, vp, i64],
         "amgf_mlp_train": [vp, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_uint64, vp],
+        "amgf_mlp_grad": [vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -240,6 +242,14 @@ def amgf_apply(h, r, z, n: int, stream=None):
     _check(load_library().amgf_apply(h, _dev_vec(r, n, "r"), _dev_vec(z, n, "z"), _stream(stream)))
 
 
+def amgf_apply_stages(h, r, z, n: int, nc: int, y1=None, r1=None, w=None, r2=None, stream=None):
+    """amgf_apply that also copies y1 = B r, r1 = r - A y1, w = A_w^{-1} P^T r1 and r2 = r1 - A P w."""
+    _check(load_library().amgf_apply_stages(
+        h, _dev_vec(r, n, "r"), _dev_vec(z, n, "z"), None if y1 is None else _dev_vec(y1, n, "y1"),
+        None if r1 is None else _dev_vec(r1, n, "r1"), None if w is None else _dev_vec(w, nc, "w"),
+        None if r2 is None else _dev_vec(r2, n, "r2"), _stream(stream)))
+
+
 def amgf_vcycle(h, r, x, n: int, stream=None):
     _check(load_library().amgf_vcycle(h, _dev_vec(r, n, "r"), _dev_vec(x, n, "x"), _stream(stream)))
 
@@ -338,6 +348,18 @@ def amgf_mlp_train(h, params, adam_m, adam_v, adam_step, iters: int, lr: float, 
     return step.value, loss[:iters]
 
 
+def amgf_mlp_grad(h, params, r_all):
+    """(loss, gradient) of the training objective for weights `params` and the concatenated
+    per-level vectors r_all (every level but the coarsest)."""
+    w = np.ascontiguousarray(params, dtype=np.float32)
+    r = np.ascontiguousarray(r_all, dtype=np.float64)
+    assert len(w) == 1313
+    g = np.zeros(1313, np.float32)
+    loss = ctypes.c_double()
+    _check(load_library().amgf_mlp_grad(h, _ptr(w), _ptr(r), _ptr(g), ctypes.byref(loss)))
+    return loss.value, g
+
+
 def amgf_destroy(h):
     if h:
         load_library().amgf_destroy(h)
@@ -377,6 +399,12 @@ class Solver:
 
     def apply(self, r, z, stream=None):
         amgf_apply(self.h, r, z, self.n, stream)
+
+    def apply_stages(self, r, z, y1=None, r1=None, w=None, r2=None, stream=None):
+        amgf_apply_stages(self.h, r, z, self.n, self.nc, y1, r1, w, r2, stream)
+
+    def mlp_grad(self, params, r_all):
+        return amgf_mlp_grad(self.h, params, r_all)
 
     def vcycle(self, r, x, stream=None):
         amgf_vcycle(self.h, r, x, self.n, stream)

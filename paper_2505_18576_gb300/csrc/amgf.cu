@@ -672,14 +672,26 @@ static void enqueue_filter_solve(Ctx& c, const double* r, const double* vdirect)
   enqueue_filter_solve_into(c, r, vdirect, c.fy, c.fz, c.fw);
 }
 
+// Copies of the intermediate vectors of one AMGF application (amgf_apply_stages); every
+// pointer may be null.  w is written in ascending-DOF order of I_c.
+struct ApplyTap {
+  double *y1 = nullptr, *r1 = nullptr, *w = nullptr, *r2 = nullptr;
+};
+
+static void tap_copy(Ctx& c, double* dst, const double* src, int64_t n) {
+  if (dst && n > 0) cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+}
+
 // z = M r; optional dot(r, z) -> *dotres.  On entry L[0].x must hold W_0 r.
-static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres) {
+static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres, const ApplyTap* tap = nullptr) {
   if (!c.o.filter) {  // M = B
     enqueue_B(c, r, z, nullptr, r, dotres);
+    if (tap) tap_copy(c, tap->y1, z, c.n);
     return;
   }
   // y1 = B r
   enqueue_B(c, r, c.y1, nullptr, nullptr, nullptr);
+  if (tap) tap_copy(c, tap->y1, c.y1, c.n);
   // r1 = r - A y1 in FP64 (and the entry state of the second V-cycle: W_0 r1, FP32 copies if
   // mixed).  This residual stays FP64 in every precision: after a good V-cycle r1 << r, and
   // its contact rows (entries up to D_max) feed the filter solve.  With K y1 in BF16 the c160
@@ -688,8 +700,11 @@ static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres) {
   ra.x = c.y1; ra.b = r; ra.y = c.r1; ra.w2 = c.L[0].winv;
   if (c.mixed) { ra.yf = c.L[0].rhsf; ra.y2f = c.L[0].xf; } else { ra.y2 = c.L[0].x; }
   launch_csr<M_RESID_W>(c, c.L[0].A, ra);
+  if (tap) tap_copy(c, tap->r1, c.r1, c.n);
   if (c.F.nc > 0) {
     enqueue_filter_solve(c, c.r1, nullptr);
+    if (tap && tap->w)
+      permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, c.ficidx, nullptr, c.fw, tap->w);
     filter_scatter_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.fgidx, c.fw, c.y1, c.F.nc);  // y2 = y1 + P w
     c.launches++;
     CsrArgs sa{};                                                                              // r2 = r1 - A P w
@@ -697,6 +712,7 @@ static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres) {
     if (c.mixed) { sa.yf = c.L[0].rhsf; sa.y2f = c.L[0].xf; } else { sa.y2 = c.L[0].x; }
     launch_csr<M_RESID_W>(c, c.fSc, sa);
   }
+  if (tap) tap_copy(c, tap->r2, c.r1, c.n);
   // z = y2 + B r2
   enqueue_B(c, c.r1, z, c.y1, r, dotres);
 }
@@ -772,16 +788,12 @@ static int apply_smoother_weights(Ctx& c, bool plain) {
   return AMGF_OK;
 }
 
-// Adam steps on the smoothing loss sum_l ||(I - A_l W_l(theta)) r_l||^2 / ||r_l||^2 (averaged over
-// the smoothed levels), r_l uniform(-1, 1) from the counter-based generator.
-static int mlp_train_impl(Ctx& c, float* params, float* adam_m, float* adam_v, int64_t* adam_step, int iters,
-                          float lr, uint64_t seed, float* loss) {
-  const int nsm = (int)c.L.size() - 1;
-  if (nsm < 1) return fail(AMGF_ERR_INVALID_ARG, "training needs at least two levels");
+// training buffers (allocated on first use)
+static int ensure_mlp_buffers(Ctx& c, int loss_cap) {
   int st;
   if (!c.mlp_m) {
     int64_t maxn = 0;
-    for (int l = 0; l < nsm; ++l) maxn = std::max<int64_t>(maxn, c.L[l].n);
+    for (int l = 0; l + 1 < (int)c.L.size(); ++l) maxn = std::max<int64_t>(maxn, c.L[l].n);
     c.mlp_part_blocks = (maxn + TPB - 1) / TPB;
     if ((st = c.alloc(&c.mlp_m, MLP_NW))) return st;
     if ((st = c.alloc(&c.mlp_v, MLP_NW))) return st;
@@ -792,10 +804,42 @@ static int mlp_train_impl(Ctx& c, float* params, float* adam_m, float* adam_v, i
     if ((st = c.alloc(&c.mlp_rr, 32))) return st;
     CK(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM));
   }
-  if (iters > c.mlp_loss_cap) {
-    if ((st = c.alloc(&c.mlp_loss, iters))) return st;
-    c.mlp_loss_cap = iters;
+  if (loss_cap > c.mlp_loss_cap) {
+    if ((st = c.alloc(&c.mlp_loss, loss_cap))) return st;
+    c.mlp_loss_cap = loss_cap;
   }
+  return AMGF_OK;
+}
+
+// Loss term and gradient of smoothed level l for the weights in c.mlp_w, with r_l already in
+// L[l].rhs: ee[l] = ||e||^2, e = (I - A_l W_l) r_l, rr[l] = ||r_l||^2, and the level's share
+// scale * d(ee/rr)/d(weights) added to c.mlp_g (written when l = 0).
+static void enqueue_mlp_level_grad(Ctx& c, int l, float scale) {
+  DLevel& lv = c.L[l];
+  const int g = vec_grid(c, lv.n);
+  dot_kernel<<<g, TPB, 0, c.s>>>(lv.n, lv.rhs, lv.rhs, c.partial, c.mlp_rr + l, c.counter);
+  mlp_infer_kernel<<<g, TPB, 0, c.s>>>(lv.n, c.feat_d[l], c.mlp_w, 0, c.l1_d[l], c.mlp_tw, nullptr);
+  scale_kernel<<<g, TPB, 0, c.s>>>(lv.n, c.mlp_tw, lv.rhs, lv.x);                    // x = W r
+  CsrArgs e{};
+  e.x = lv.x; e.b = lv.rhs; e.y = lv.res;
+  launch_csr<M_RESID>(c, lv.A, e, lv.res, c.mlp_ee + l);                            // e = r - A x
+  CsrArgs ae{};
+  ae.x = lv.res; ae.y = lv.out;
+  launch_csr<M_SPMV>(c, lv.A, ae);                                                   // A e
+  const int nb = (int)((lv.n + TPB - 1) / TPB);
+  mlp_backward_kernel<<<nb, TPB, MLP_SMEM, c.s>>>(lv.n, c.feat_d[l], c.mlp_w, lv.rhs, c.l1_d[l], lv.out,
+                                                  c.mlp_rr + l, scale, c.mlp_part);
+  mlp_grad_reduce_kernel<<<(MLP_NW + TPB - 1) / TPB, TPB, 0, c.s>>>(nb, c.mlp_part, c.mlp_g, l > 0 ? 1 : 0);
+}
+
+// Adam steps on the smoothing loss sum_l ||(I - A_l W_l(theta)) r_l||^2 / ||r_l||^2 (averaged over
+// the smoothed levels), r_l uniform(-1, 1) from the counter-based generator.
+static int mlp_train_impl(Ctx& c, float* params, float* adam_m, float* adam_v, int64_t* adam_step, int iters,
+                          float lr, uint64_t seed, float* loss) {
+  const int nsm = (int)c.L.size() - 1;
+  if (nsm < 1) return fail(AMGF_ERR_INVALID_ARG, "training needs at least two levels");
+  int st = ensure_mlp_buffers(c, iters);
+  if (st) return st;
   CK(cudaMemcpyAsync(c.mlp_w, params, MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
   CK(cudaMemcpyAsync(c.mlp_m, adam_m, MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
   CK(cudaMemcpyAsync(c.mlp_v, adam_v, MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
@@ -804,22 +848,9 @@ static int mlp_train_impl(Ctx& c, float* params, float* adam_m, float* adam_v, i
   for (int it = 0; it < iters; ++it) {
     for (int l = 0; l < nsm; ++l) {
       DLevel& lv = c.L[l];
-      const int g = vec_grid(c, lv.n);
       const uint64_t sd = seed ^ (0x632BE59BD9B4E019ull * (uint64_t)(t + 1)) ^ ((uint64_t)l << 56);
-      rand_uniform_kernel<<<g, TPB, 0, c.s>>>(lv.n, sd, lv.rhs);                       // r
-      dot_kernel<<<g, TPB, 0, c.s>>>(lv.n, lv.rhs, lv.rhs, c.partial, c.mlp_rr + l, c.counter);
-      mlp_infer_kernel<<<g, TPB, 0, c.s>>>(lv.n, c.feat_d[l], c.mlp_w, 0, c.l1_d[l], c.mlp_tw, nullptr);
-      scale_kernel<<<g, TPB, 0, c.s>>>(lv.n, c.mlp_tw, lv.rhs, lv.x);                    // x = W r
-      CsrArgs e{};
-      e.x = lv.x; e.b = lv.rhs; e.y = lv.res;
-      launch_csr<M_RESID>(c, lv.A, e, lv.res, c.mlp_ee + l);                            // e = r - A x
-      CsrArgs ae{};
-      ae.x = lv.res; ae.y = lv.out;
-      launch_csr<M_SPMV>(c, lv.A, ae);                                                   // A e
-      const int nb = (int)((lv.n + TPB - 1) / TPB);
-      mlp_backward_kernel<<<nb, TPB, MLP_SMEM, c.s>>>(lv.n, c.feat_d[l], c.mlp_w, lv.rhs, c.l1_d[l], lv.out,
-                                                      c.mlp_rr + l, scale, c.mlp_part);
-      mlp_grad_reduce_kernel<<<(MLP_NW + TPB - 1) / TPB, TPB, 0, c.s>>>(nb, c.mlp_part, c.mlp_g, l > 0 ? 1 : 0);
+      rand_uniform_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, sd, lv.rhs);       // r
+      enqueue_mlp_level_grad(c, l, scale);
     }
     mlp_loss_kernel<<<1, 1, 0, c.s>>>(nsm, c.mlp_ee, c.mlp_rr, scale, c.mlp_loss + it);
     ++t;
@@ -834,6 +865,34 @@ static int mlp_train_impl(Ctx& c, float* params, float* adam_m, float* adam_v, i
   CK(cudaStreamSynchronize(c.s));
   *adam_step = t;
   // the level operators' W stay those of the active weights
+  return apply_smoother_weights(c, false);
+}
+
+// Loss and gradient of the training objective for given weights and given r_l (the kernels of
+// one training step without the Adam update).
+static int mlp_grad_impl(Ctx& c, const float* params, const double* r_all, float* grad, double* loss) {
+  const int nsm = (int)c.L.size() - 1;
+  if (nsm < 1) return fail(AMGF_ERR_INVALID_ARG, "the loss needs at least two levels");
+  int st = ensure_mlp_buffers(c, 1);
+  if (st) return st;
+  CK(cudaMemcpyAsync(c.mlp_w, params, MLP_NW * sizeof(float), cudaMemcpyHostToDevice, c.s));
+  const float scale = 1.0f / (float)nsm;
+  int64_t off = 0;
+  for (int l = 0; l < nsm; ++l) {
+    DLevel& lv = c.L[l];
+    CK(cudaMemcpyAsync(lv.rhs, r_all + off, (size_t)lv.n * sizeof(double), cudaMemcpyHostToDevice, c.s));
+    off += lv.n;
+    enqueue_mlp_level_grad(c, l, scale);
+  }
+  CK(cudaGetLastError());
+  std::vector<double> ee(nsm), rr(nsm);
+  CK(cudaMemcpyAsync(grad, c.mlp_g, MLP_NW * sizeof(float), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(ee.data(), c.mlp_ee, nsm * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaMemcpyAsync(rr.data(), c.mlp_rr, nsm * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  CK(cudaStreamSynchronize(c.s));
+  double sum = 0.0;
+  for (int l = 0; l < nsm; ++l) sum += ee[l] / rr[l];
+  if (loss) *loss = sum / nsm;
   return apply_smoother_weights(c, false);
 }
 
@@ -1550,6 +1609,24 @@ int amgf_apply(amgf_handle h, const double* r_dev, double* z_dev, void* stream) 
   return join_end(c, stream);
 }
 
+int amgf_apply_stages(amgf_handle h, const double* r_dev, double* z_dev, double* y1_dev, double* r1_dev,
+                      double* w_dev, double* r2_dev, void* stream) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !r_dev || !z_dev || r_dev == z_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  if ((w_dev || r2_dev) && (!c.o.filter || c.F.nc == 0))
+    return fail(AMGF_ERR_INVALID_ARG, "w and r2 need the filter (options.filter = 1, nonempty I_c)");
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  ApplyTap tap;
+  tap.y1 = y1_dev; tap.r1 = r1_dev; tap.w = w_dev; tap.r2 = r2_dev;
+  enqueue_scale_w0(c, r_dev);
+  enqueue_apply(c, r_dev, z_dev, nullptr, &tap);
+  CK(cudaGetLastError());
+  return join_end(c, stream);
+}
+
 int amgf_vcycle(amgf_handle h, const double* r_dev, double* x_dev, void* stream) {
   if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
   if (!h || !r_dev || !x_dev || r_dev == x_dev) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
@@ -1620,7 +1697,17 @@ static int solve_device(Ctx& c, amgf_stats* stats) {
     }
   }
   CK(cudaEventRecord(c.t1, c.s));
+  // true residual of the returned iterate: q = b - A x (FP64), ||q||^2 and ||b||^2
+  {
+    CsrArgs ra{};
+    ra.x = c.x; ra.b = c.b; ra.y = c.q;
+    launch_csr<M_RESID>(c, c.L[0].A, ra);
+    dot_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.q, c.q, c.partial, c.scratch_scalar + 2, c.counter);
+    dot_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.b, c.b, c.partial, c.scratch_scalar + 3, c.counter);
+  }
   CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(PcgState), cudaMemcpyDeviceToHost, c.s));
+  double res2[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(res2, c.scratch_scalar + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
   CK(cudaGetLastError());
   float ms = 0.f;
@@ -1638,6 +1725,8 @@ static int solve_device(Ctx& c, amgf_stats* stats) {
     // when the initial residual already meets the stop test)
     const int64_t trips = s.iter > 0 ? s.iter : (c.o.use_graph ? 1 : 0);
     stats->kernel_launches = c.init_launches + trips * c.body_launches;
+    stats->rel_res_l2 = res2[1] > 0.0 ? std::sqrt(res2[0] / res2[1]) : 0.0;
+    stats->t_setup_s = c.info.t_setup_s;
   }
   if (s.status != 0) {
     static const char* names[] = {"ok", "invalid", "non-finite PCG scalar", "not SPD", "breakdown (p^T A p <= 0 or r^T z < 0)",
@@ -1714,6 +1803,14 @@ int amgf_mlp_train(amgf_handle h, float* params, float* adam_m, float* adam_v, i
   return mlp_train_impl(h->c, params, adam_m, adam_v, adam_step, iters, lr, seed, loss);
 }
 
+int amgf_mlp_grad(amgf_handle h, const float* params, const double* r_all, float* grad, double* loss) {
+  if (!h || !params || !r_all || !grad) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  if (h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (h->c.mixed) return fail(AMGF_ERR_INVALID_ARG, "the training loss runs on an FP64 handle (precision 0)");
+  CK(cudaSetDevice(h->c.device));
+  return mlp_grad_impl(h->c, params, r_all, grad, loss);
+}
+
 int amgf_get_info(amgf_handle h, amgf_info* info) {
   if (!h || !info) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
   *info = h->c.info;
@@ -1744,9 +1841,10 @@ int amgf_export_contact_set(amgf_handle h, int64_t* ic) {
 
 int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* stream, double* ms, double* bytes) {
   if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
-  if (!h || !ms || !bytes || reps < 1 || warmup < 0 || which < 0 || which > 2)
+  if (!h || !ms || !bytes || reps < 1 || warmup < 0 || which < 0 || which > 3)
     return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
   if (which == 2 && !h->c.mixed) return fail(AMGF_ERR_INVALID_ARG, "which = 2 needs a mixed-precision handle");
+  if (which == 3 && h->c.L.size() < 3) return fail(AMGF_ERR_INVALID_ARG, "which = 3 needs >= 3 levels");
   Ctx& c = h->c;
   CK(cudaSetDevice(c.device));
   int st = join_begin(c, stream);
@@ -1754,7 +1852,18 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
   DLevel& l0 = c.L[0];
   const double nnz = (double)l0.A.nnz, n = (double)l0.n;
   auto launch = [&]() {
-    if (which == 2) {
+    if (which == 3) {  // level-1 post-smoother in the V-cycle's precision
+      DLevel& l1 = c.L[1];
+      if (c.mixed) {
+        CsrArgsT<float> a{};
+        a.x = l1.xf; a.b = l1.rhsf; a.winv = l1.winvf; a.y = l1.outf;
+        launch_csr_f<M_POST>(c, l1.Af, a);
+      } else {
+        CsrArgs a{};
+        a.x = l1.x; a.b = l1.rhs; a.winv = l1.winv; a.y = l1.out;
+        launch_csr<M_POST>(c, l1.A, a);
+      }
+    } else if (which == 2) {
       launch_fine_mixed<M_POST>(c, l0.xf, l0.rhsf, l0.winvf, nullptr, nullptr, c.q, nullptr, nullptr);
     } else if (which == 0) {
       CsrArgs a{};
@@ -1776,7 +1885,12 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
   *ms = t / reps;
   // values (8 B) + column indices (4 B) per nonzero, row pointers, and each vector read/written once
   const double vec_bytes = which == 0 ? 2.0 * 8.0 * n : 4.0 * 8.0 * n;
-  if (which == 2) {  // K blocks (4 or 2 bytes per value + index), contact CSR, 3 FP32 reads + FP64 write
+  if (which == 3) {  // values (8, 4 or 2 B) + 4 B column per nonzero, row pointers, x, b, W, y
+    const DLevel& l1 = c.L[1];
+    const double vb = c.mixed ? (l1.Af.vb ? 2.0 : 4.0) : 8.0, eb = c.mixed ? 4.0 : 8.0;
+    const double nz1 = (double)(c.mixed ? l1.Af.nnz : l1.A.nnz), n1 = (double)l1.n;
+    *bytes = nz1 * (vb + 4.0) + (n1 + 1.0) * 8.0 + 4.0 * eb * n1;
+  } else if (which == 2) {  // K blocks (4 or 2 bytes per value + index), contact CSR, 3 FP32 reads + FP64 write
     const double vb = c.k_bf16 ? 2.0 : 4.0;
     *bytes = (double)c.k_nblocks * (9.0 * vb + 4.0) + (double)(c.k_nslices + 1) * 8.0 + (n + 1) * 4.0 +
              3.0 * 4.0 * n + 8.0 * n;

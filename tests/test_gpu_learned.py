@@ -99,3 +99,42 @@ def test_fallback_to_plain_weights(prob):
     x.zero_()
     st = s2.pcg_solve(dev(prob.b), x)
     assert st.status == 0 and st.mlp_fallback == 1 and st.iters == k_plain
+
+
+def test_training_gradient_matches_oracle_finite_differences(tiny):
+    # The device gradient of the training objective (mlp_backward_kernel, summed over levels by
+    # mlp_grad_reduce_kernel) for given weights and given r_l, against central differences of
+    # the oracle's FP64 objective (pinned there by the closed form on Fourier modes) for all
+    # 1313 weights.  The step h = 1e-4 keeps the differences within ~2e-4 max|g| of the
+    # derivative (ReLU kinks crossed by the step); the device computes the MLP in FP32.
+    import paper_2505_18576_gb300 as m
+    s = m.Solver(tiny.K, tiny.J, tiny.D, max_coarse=128)
+    o = oracle.Oracle(tiny.K, tiny.J, tiny.D, max_coarse=128)
+    ns = [int(s.info.level_rows[l]) for l in range(s.info.nlevels - 1)]
+    assert ns == [o.A(l).shape[0] for l in range(o.nlev - 1)] and len(ns) >= 2
+    rng = np.random.default_rng(11)
+    w = (rng.standard_normal(1313) * 0.5).astype(np.float32)
+    r = rng.uniform(-1, 1, sum(ns))
+    loss, g = s.mlp_grad(w, r)
+    w64 = w.astype(np.float64)
+    o.set_mlp(w64)
+    lo = o.mlp_loss(r)
+    assert abs(loss - lo) <= 1e-5 * lo
+    h = 1e-4
+    fd = np.zeros(1313)
+    for k in range(1313):
+        wp = w64.copy(); wp[k] += h
+        o.set_mlp(wp)
+        lp = o.mlp_loss(r)
+        wp[k] -= 2 * h
+        o.set_mlp(wp)
+        fd[k] = (lp - o.mlp_loss(r)) / (2 * h)
+    gmax = np.abs(fd).max()
+    err = np.abs(g.astype(np.float64) - fd)
+    print(f"gradient: max|g| {gmax:.3e}, max abs diff {err.max():.3e}, loss {loss:.6f} (oracle {lo:.6f})")
+    assert gmax > 0 and np.all(err <= 2e-3 * gmax + 2e-2 * np.abs(fd))
+    # a learning-rate-scaled step along -g lowers the oracle's objective
+    o.set_mlp(w64 - 1e-2 * g.astype(np.float64) / gmax)
+    assert o.mlp_loss(r) < lo
+    s.close()
+    o.close()

@@ -14,7 +14,8 @@ tests/test_library_host.py, so every difference comes from the order of operatio
     D in [1, 10] (kappa(A_w) u < 1e-13) asserts the strict 1e-12.
   - PCG at rtol 1e-8: iteration counts within +-1, and ||x_gpu - x_orc||_A <= 2 rtol sqrt(kappa(MA))
     ||x_orc||_A (each iterate's A-norm error is at most rtol sqrt(kappa(MA)) ||x*||_A when
-    lambda_max(MA) <= 1, x0 = 0); at rtol 1e-12 the A-norm difference is at most
+    lambda_max(MA) <= 1, x0 = 0), or 10 f where the rounding floor f (below) is larger (D up to
+    1e12: f ~ 5e-5-8e-5 on these meshes); at rtol 1e-12 the A-norm difference is at most
     max(1e-8, 10 f), f = the FP64 rounding floor of the solve, measured as the A-norm spread of
     two oracle solves whose starting guesses differ by 1e-10 |b| (entries of A reach
     D_max ~ 1e8 while |x| ~ 1e2, so the true residual stalls near u |A||x| and two exact-
@@ -59,6 +60,11 @@ CASES = {
     "ragged": dict(nx=5, ny=3, nz=2, d_lo=-2, d_hi=8),
     "n16": dict(nx=16, ny=12, nz=7, d_lo=-2, d_hi=8),
     "n16_deep": dict(nx=16, ny=12, nz=7, d_lo=-2, d_hi=8),
+    # the full-form barrier range, D up to 1e12: kappa(A_w) ~ 1e14, so the forward bounds of the
+    # filter and the apply below are loose there; tests/test_gpu_stages.py checks every step of
+    # the apply on these systems with kappa-free bounds
+    "n16_d12": dict(nx=16, ny=12, nz=7, d_lo=-2, d_hi=12),
+    "n24_d12": dict(nx=24, ny=24, nz=12, d_lo=-2, d_hi=12),
 }
 # the default hierarchy (coarsest <= 1200 rows, 4 weights per interpolation row) has two to
 # four levels on these sizes; n16_deep keeps coarsening to 128 rows without truncation, so
@@ -186,7 +192,10 @@ def test_pcg_parity(case):
     assert abs(st.iters - ko) <= 1
     kap, _, _ = kappa_estimate(al, be)
     S = o.S()
-    assert a_norm(S, host(x) - xo) <= 2e-8 * np.sqrt(kap) * a_norm(S, xo)
+    # with D up to 1e12 the FP64 rounding floor f of the A-norm comparison (two oracle solves
+    # started 1e-10 |b| apart) lies above 2 rtol sqrt(kappa): u D_max |x| in the contact rows
+    floor = rounding_floor(o, p.b, xo, 1e-8) if CASES[name]["d_hi"] > 8 else 0.0
+    assert a_norm(S, host(x) - xo) <= max(2e-8 * np.sqrt(kap), 10 * floor) * a_norm(S, xo)
 
 
 def rounding_floor(o, b, xo, tol):

@@ -1,27 +1,34 @@
 #!/usr/bin/env python
 """Benchmark: AMGF-PCG seconds to a relative preconditioned residual of 1e-8 on one GB300.
 
-Workload (default): the c64 two-block contact system -- two stacked Q1 linear-elastic
-blocks of 64x64x32 elements each (E=1, nu=0.3), node-to-node normal contact on the
-65x65 interface (m=4225), barrier diagonal D log-uniform in [1e-2, 1e8], n=811,200
-DOFs, three seeded right-hand sides (seeds 0, 1, 2) cycled over the steps.  Synthetic
-data from contactgen (seeded); FP64 arithmetic throughout.
+Workload (default, the full form): the c160 two-block contact system -- two stacked Q1
+linear-elastic blocks of 160x160x80 elements each (E=1, nu=0.3), node-to-node normal contact
+on the 161x161 interface (m=25,921), barrier diagonal D log-uniform in [1e-2, 1e12],
+n=12,442,080 DOFs, three seeded right-hand sides (seeds 0, 1, 2) cycled over the steps.
+Synthetic data from contactgen (seeded).
 
-One step = one full AMGF-PCG solve (x0 = 0) through the C ABI with inputs resident in
-HBM.  The working set (fine operator ~0.76 GB plus hierarchy) is larger than L2, so
-no flush is needed between steps.  Prints one JSON line (rank 0).  Besides the
-contract's keys it carries `variants` (the other V-cycle precisions and the learned
-smoother on the same workload, each with its A-norm distance to the timed solution) and
-`a_norm_rounding_floor` (the A-norm distance between two FP64-equivalent solves started
-1e-10 |b| apart: the scale below which solutions cannot be told apart in FP64).
+One step = one full AMGF-PCG solve (x0 = 0) through the C ABI with inputs resident in HBM;
+`value` is the plain FP64 solve (FP64 V-cycle, l1-Jacobi smoother with theta = 1).  The
+working set (fine operator 8.6 GB plus hierarchy) is far larger than L2, so no flush is needed
+between steps.  Prints one JSON line (rank 0).  Besides the contract's keys it carries
+  - `variants`: the other V-cycle precisions and the learned smoother on the same workload
+    (default: the mixed-precision + learned-smoother form, FP32 arithmetic with BF16 storage of
+    every V-cycle matrix), each with its seconds per solve, PCG iterations, A-norm distance to
+    the FP64 solution, true residual and the roofline of its dominant kernels;
+  - `a_norm_rounding_floor`: the A-norm distance between two FP64 solves started 1e-10 |b|
+    apart, the scale below which solutions cannot be told apart in FP64;
+  - `roofline` (the FP64 fine-level sweep against the measured HBM copy bandwidth, with its
+    FP64-pipe fraction as a secondary figure) and `roofline_coarse` (the level-1 sweep);
+  - `cpu_baseline`: the CPU FP64 oracle on the host cores -- one complete PCG solve of the
+    same system on all cores (setup reported separately) and a single-threaded sample.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amgf|reference] [--config c64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl amgf|reference] [--config c160]
 
---impl reference times the CPU FP64 oracle on the host cores on a bounded sample of
-the same workload (a few PCG iterations per step, scaled to the full solve's
-iteration count).  Under torchrun with N > 1 the GPU arm runs N independent replicas
-(the solve does not shard; no collective on the data path); the reference arm runs
-on rank 0 only.
+--impl reference times the CPU FP64 oracle on the host cores: each step runs a bounded
+sample of PCG iterations of the same system, scaled to the full solve's iteration count
+(`ms_per_step` is the measured time of a sampled step); one complete solve is timed as
+well.  Under torchrun with N > 1 the GPU arm runs N independent replicas (the solve does
+not shard; no collective on the data path); the reference arm runs on rank 0 only.
 """
 from __future__ import annotations
 
@@ -40,25 +47,44 @@ if ROOT not in sys.path:
 
 METRIC = "AMGF-PCG seconds to 1e-8 rel. residual"
 WORKLOADS = {
+    "tiny": "two-block Q1 elasticity, 8x8x4 elements per block, n=1944, m=81 node-to-node contact rows, "
+            "D log-uniform [1e-2,1e4]",
     "c64": "two-block Q1 elasticity, 64x64x32 elements per block, n=811200, m=4225 node-to-node contact rows, "
-           "D log-uniform [1e-2,1e8], 3 seeded RHS, FP64 AMGF-PCG",
-    "tiny": "two-block Q1 elasticity, 8x8x4 elements per block, n=1944, m=81, D log-uniform [1e-2,1e4]",
-    "c96": "two-block Q1 elasticity, 96x96x48 elements per block, n=2709792, m=9409, D log-uniform [1e-2,1e10], "
-           "FP64 AMGF-PCG",
-    "c160": "two-block Q1 elasticity, 160x160x80 elements per block, n=12442080, m=25921, D log-uniform "
-            "[1e-2,1e12], FP64 AMGF-PCG",
-    "c202": "two-block Q1 elasticity, 202x202x101 elements per block, n=24972654, m=41209, D log-uniform "
-            "[1e-2,1e12], FP64 AMGF-PCG",
+           "D log-uniform [1e-2,1e8], 3 seeded RHS",
+    "c96": "two-block Q1 elasticity, 96x96x48 elements per block, n=2709792, m=9409 node-to-node contact rows, "
+           "D log-uniform [1e-2,1e10], 3 seeded RHS",
+    "c160": "two-block Q1 elasticity, 160x160x80 elements per block, n=12442080, m=25921 node-to-node contact "
+            "rows, D log-uniform [1e-2,1e12], 3 seeded RHS",
+    "c202": "two-block Q1 elasticity, 202x202x101 elements per block, n=24972654, m=41209 node-to-node contact "
+            "rows, D log-uniform [1e-2,1e12], 3 seeded RHS",
 }
+PRECISIONS = ["FP64 V-cycle", "FP32 V-cycle", "FP32 V-cycle with BF16 fine-level K",
+              "FP32 V-cycle with BF16 storage of every V-cycle matrix"]
+# variant name -> (precision, learned smoother)
+VARIANTS = {"fp64": (0, False), "fp32_vcycle": (1, False), "fp32_vcycle_bf16_K": (2, False),
+            "fp32_vcycle_bf16_all": (3, False), "fp32_vcycle_bf16_K_learned": (2, True),
+            "fp32_vcycle_bf16_all_learned": (3, True)}
+DEFAULT_VARIANTS = "fp32_vcycle_bf16_all_learned"
 # learned smoother weights trained by `python -m paper_2505_18576_gb300.learned --config c64 --out ...`
 WEIGHTS = os.path.join(ROOT, "paper_2505_18576_gb300", "weights", "smoother_c64.npz")
 
 
-def workload_name(args) -> str:
+def method_label(precision: int, learned: bool) -> str:
+    smoother = "learned l1-Jacobi damping (MLP)" if learned else "l1-Jacobi, theta = 1"
+    return f"AMGF-PCG in FP64 (flexible when mixed), {PRECISIONS[precision]}, {smoother}"
+
+
+def workload_name(args, precision: int = 0, learned: bool = False) -> str:
     name = f"{args.config}: {WORKLOADS.get(args.config, args.config)}"
     if args.curvature:
         name += f"; contact along the normals of a curved interface (curvature {args.curvature:g})"
-    return name
+    return name + "; " + method_label(precision, learned)
+
+
+def shared_config(args, p, precision: int = 0, learned: bool = False) -> dict:
+    """`config` of both arms: the workload and the stop test (no implementation keys)."""
+    return {"workload": workload_name(args, precision, learned), "n": int(p.n), "m": int(p.m), "rtol": 1e-8,
+            "stop": "sqrt(r^T z / r0^T z0)", "l2": "working set larger than L2 (no flush)"}
 
 
 def dist_env():
@@ -136,20 +162,50 @@ def make_inputs(config: str, curvature: float = 0.0):
     return p, rhs
 
 
-def cpu_oracle_sample(p, rhs, iters_full: float, sample_iters: int, reps: int = 1):
-    """Time `sample_iters` oracle PCG iterations (after its setup); scale to a full solve."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_baseline(p, rhs):
+    """The CPU FP64 oracle on this host: setup, one complete PCG solve of seed 0's system on all
+    cores, and a single-threaded sample (the initial residual, apply and one iteration) scaled by
+    the all-core ratio of the complete solve to the same sample."""
     import oracle
+    cores = os.cpu_count()
+    threads = oracle.set_threads(0)
     t0 = time.perf_counter()
     o = oracle.Oracle(p.K, p.J, p.D)
     t_setup = time.perf_counter() - t0
-    per_iter = []
-    for k in range(reps):
-        t0 = time.perf_counter()
-        o.pcg(rhs[k % len(rhs)], tol=1e-30, maxit=sample_iters)
-        per_iter.append((time.perf_counter() - t0) / sample_iters)
-    sec_iter = statistics.median(per_iter)
+    t0 = time.perf_counter()
+    _, k_full, st, *_ = o.pcg(rhs[0], tol=1e-8)
+    t_full = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.pcg(rhs[0], tol=1e-30, maxit=1)
+    t_one_all = time.perf_counter() - t0
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    o.pcg(rhs[0], tol=1e-30, maxit=1)
+    t_one_single = time.perf_counter() - t0
+    oracle.set_threads(threads)
     o.close()
-    return sec_iter * iters_full, sec_iter, t_setup
+    single = t_one_single * (t_full / t_one_all)
+    return {"value": t_full, "unit": "s", "cores": threads, "kind": "oracle",
+            "sample": f"one complete oracle AMGF-PCG solve of the {p.n}-DOF system (seed 0), {k_full} iterations, "
+                      f"status {st}, on {threads} threads; oracle setup {t_setup:.1f} s reported separately",
+            "setup_s": round(t_setup, 2), "pcg_iters": int(k_full), "cpu_model": cpu_model(),
+            "host_cores": cores,
+            "single_thread": {"value": single, "unit": "s", "cores": 1,
+                              "sample": f"initial residual, preconditioner apply and one PCG iteration on one "
+                                        f"thread ({t_one_single:.2f} s; {t_one_all:.2f} s on {threads} threads), "
+                                        f"scaled by the complete solve's time over the same sample on {threads} "
+                                        f"threads"}}
 
 
 def max_over_ranks(values, dist, device):
@@ -163,33 +219,90 @@ def max_over_ranks(values, dist, device):
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores: K steps of a bounded sample of PCG iterations each."""
     if rank != 0:
         return 0
     import oracle
     p, rhs = make_inputs(args.config, args.curvature)
-    cores = os.cpu_count()
+    threads = oracle.set_threads(0)
+    t0 = time.perf_counter()
     o = oracle.Oracle(p.K, p.J, p.D)
-    # iteration count of the full solve (untimed, once): scales the per-iteration sample
+    t_setup = time.perf_counter() - t0
+    # one complete solve (untimed by the steps): the iteration count that scales each sample
+    t0 = time.perf_counter()
     _, k_full, st, *_ = o.pcg(rhs[0], tol=1e-8)
-    times = []
+    t_full = time.perf_counter() - t0
+    k = max(1, args.ref_iters)
+    times, step_s = [], []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        o.pcg(rhs[step % 3], tol=1e-30, maxit=args.ref_iters)
+        o.pcg(rhs[step % 3], tol=1e-30, maxit=k)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
-            times.append(dt / args.ref_iters * k_full)
+            step_s.append(dt)
+            # the sample's initial residual and preconditioner apply cost about one iteration
+            times.append(dt / (k + 1) * (k_full + 1))
+    o.close()
     value = statistics.mean(times)
-    sample = (f"{args.ref_iters} PCG iterations of the {args.config} solve per step (oracle setup excluded), "
-              f"scaled by the full solve's {k_full} iterations")
+    sample = (f"{k} oracle PCG iterations of the {args.config} solve per step after the initial residual and "
+              f"preconditioner apply (oracle setup excluded), scaled by (k_full + 1) / ({k} + 1) with the complete "
+              f"solve's k_full = {k_full} iterations; ms_per_step is the measured time of a sampled step")
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_name(args), "rtol": 1e-8,
-                       "stop": "sqrt(r^T z / r0^T z0)", "parallelism": "host cores (OpenMP row loops)"},
-            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_s) * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": shared_config(args, p),
+            "parallelism": f"host cores ({threads} OpenMP threads)",
+            "value_kind": "extrapolated from the sampled steps",
+            "complete_solve": {"s": t_full, "pcg_iters": int(k_full), "status": int(st),
+                               "setup_s": round(t_setup, 2)},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def load_traffic(kind: str, precision: int, bytes_now: float):
+    """DRAM bytes per launch of a kernel, from the ncu capture stored in profiles/: the ratio of
+    measured DRAM bytes to algorithmic bytes at the captured size, times this launch's algorithmic
+    bytes.  None when the kernel's source changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            tr = json.load(f)
+        ent = tr.get(f"{kind}:precision{precision}")
+        if not ent or ent.get("kernel_source_sha") != kernel_source_sha(kind, precision):
+            return None, None
+        ratio = ent["dram_bytes_per_launch"] / ent["algorithmic_bytes_per_launch"]
+        return ratio * bytes_now, f"{ent['capture']} (DRAM / algorithmic = {ratio:.3f}, scaled to this launch)"
+    except Exception:
+        return None, None
+
+
+def roofline_of(s, which: int, kind: str, precision: int, hbm_peak: float, peak_kind: str, sm_count: int,
+                sm_mhz: float, label: str):
+    kms, kbytes = s.time_kernel(which, warmup=5, reps=50)
+    gbs = kbytes / (kms * 1e-3) / 1e9
+    traffic, tsrc = load_traffic(kind, precision, kbytes)
+    out = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+           "frac": round(gbs / hbm_peak, 4), "traffic": None if traffic is None else round(traffic),
+           "kernel": label, "bytes_per_launch": kbytes, "ms_per_launch": kms,
+           "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs, burst)"}
+    if tsrc:
+        out["traffic_source"] = tsrc
+    if precision == 0:
+        if which == 3:
+            nnz = float(s.info.level_nnz[1])
+            rows = float(s.info.level_rows[1])
+        else:
+            nnz = float(s.info.level_nnz[0])
+            rows = float(s.info.n)
+        flops = 2.0 * nnz + 4.0 * rows        # one FMA per nonzero; b - s, * w, + x, + add per row
+        peak = sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12
+        tf = flops / (kms * 1e-3) / 1e12
+        out["fp64_pipe"] = {"achieved": round(tf, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                            "frac": round(tf / peak, 4),
+                            "peak_kind": f"derived: {sm_count} SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz"}
+    return out
 
 
 def run_gpu(args, rank, world, local):
@@ -197,6 +310,7 @@ def run_gpu(args, rank, world, local):
     import torch
 
     import paper_2505_18576_gb300 as amgf
+    from paper_2505_18576_gb300.learned import load_weights
 
     torch.cuda.set_device(local)
     dist = None
@@ -209,15 +323,22 @@ def run_gpu(args, rank, world, local):
         if dist is not None:
             dist.barrier()
 
+    props = torch.cuda.get_device_properties(local)
+    sm_count = int(props.multi_processor_count)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            sm_mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        sm_mhz = 2070.0
+    hbm_peak, peak_kind = peaks()
+
     p, rhs = make_inputs(args.config, args.curvature)
+    learned = bool(args.weights)
     t0 = time.perf_counter()
     s = amgf.Solver(p.K, p.J, p.D, use_graph=0 if args.no_graph else 1, precision=args.precision)
     t_setup = time.perf_counter() - t0
-    weights = None
-    if args.weights:
-        from paper_2505_18576_gb300.learned import load_weights
-        weights = load_weights(WEIGHTS if args.weights == "default" else args.weights)
-        s.set_mlp(weights)
+    if learned:
+        s.set_mlp(load_weights(WEIGHTS if args.weights == "default" else args.weights))
     info = s.info
     n = p.n
     bdev = [torch.from_numpy(b).cuda() for b in rhs]
@@ -228,14 +349,13 @@ def run_gpu(args, rank, world, local):
         s.pcg_solve(bdev[k % 3], x)
     torch.cuda.synchronize()
 
-    props = torch.cuda.get_device_properties(local)
     bus = getattr(props, "pci_bus_id", None)
     sampler = ClockSampler(None if bus is None else str(bus))
     sampler.start()
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters, launches, solve_s, fallbacks = [], 0, [], 0
+    iters, launches, fallbacks, relres = [], 0, 0, []
     ev0.record(stream)
     for k in range(args.steps):
         x.zero_()
@@ -243,7 +363,7 @@ def run_gpu(args, rank, world, local):
         iters.append(st.iters)
         fallbacks += st.mlp_fallback
         launches += st.kernel_launches
-        solve_s.append(st.t_solve_s)
+        relres.append(st.rel_res_l2)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -263,171 +383,149 @@ def run_gpu(args, rank, world, local):
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e_s = max_over_ranks([e2e_s], dist, "cuda")[0]
 
-    # the same workload with the other V-cycle precisions (same timing method, fewer steps),
-    # each with its A-norm distance to this run's solution of seed 0
-    variants = {}
-    floor = None
-    if not args.no_variants:
-        x_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
-        s.pcg_solve(bdev[0], x_ref)
-        table = [("fp64", 0, False), ("fp32_vcycle", 1, False), ("fp32_vcycle_bf16_K", 2, False),
-                 ("fp32_vcycle_bf16_all", 3, False)]
-        if os.path.exists(WEIGHTS):
-            table += [("fp32_vcycle_bf16_K_learned", 2, True), ("fp32_vcycle_bf16_all_learned", 3, True)]
-        wanted = None if args.variants == "all" else set(args.variants.split(","))
-        for name, prec, learned in table:
-            if (prec, learned) == (args.precision, weights is not None) or (wanted and name not in wanted):
-                continue
-            sv = amgf.Solver(p.K, p.J, p.D, precision=prec)
-            if learned:
-                from paper_2505_18576_gb300.learned import load_weights
-                sv.set_mlp(load_weights(WEIGHTS))
-            xv = torch.zeros(n, dtype=torch.float64, device="cuda")
-            for k in range(2):
-                xv.zero_()
-                sv.pcg_solve(bdev[k % 3], xv)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            its, fb = [], 0
-            nst = max(2, min(args.steps, 5))
-            e0.record(stream)
-            for k in range(nst):
-                xv.zero_()
-                stv = sv.pcg_solve(bdev[k % 3], xv, stream=stream)
-                its.append(stv.iters)
-                fb += stv.mlp_fallback
-            e1.record(stream)
-            torch.cuda.synchronize()
+    # dominant kernels: the fine-level l1-Jacobi post-smoother (one pass over the fine operator with
+    # the fused smoother epilogue) and the level-1 post-smoother, each timed alone with CUDA events
+    fine_label = ("bsr3_kernel<POST>: fine-level FP64 l1-Jacobi sweep over A (3x3 node blocks)" if args.precision == 0
+                  else "bsr3_mixed_kernel<POST>: fine-level FP32 l1-Jacobi sweep (K blocks + FP64 contact term)")
+    roofline = roofline_of(s, 1 if args.precision == 0 else 2, "fine", args.precision, hbm_peak, peak_kind,
+                           sm_count, sm_mhz, fine_label)
+    roofline_coarse = None
+    if info.nlevels >= 3:
+        roofline_coarse = roofline_of(s, 3, "level1", args.precision, hbm_peak, peak_kind, sm_count, sm_mhz,
+                                      f"csr_kernel<POST>: level-1 l1-Jacobi sweep ({PRECISIONS[args.precision]})")
+
+    # the same workload with the other V-cycle precisions / the learned smoother (same timing method,
+    # fewer steps), each with its A-norm distance to the timed configuration's solution of seed 0
+    variants, floor = {}, None
+    wanted = [] if args.variants == "none" else (list(VARIANTS) if args.variants == "all"
+                                                   else args.variants.split(","))
+    x_ref = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st_ref = s.pcg_solve(bdev[0], x_ref)
+
+    def a_norm_rel(xv):
+        d = xv - x_ref
+        yd = torch.empty_like(d)
+        yr = torch.empty_like(d)
+        s.matvec(d, yd)
+        s.matvec(x_ref, yr)
+        return float(torch.sqrt(torch.dot(d, yd) / torch.dot(x_ref, yr)))
+
+    for name in wanted:
+        prec, lrn = VARIANTS[name]
+        if (prec, lrn) == (args.precision, learned) or (lrn and not os.path.exists(WEIGHTS)):
+            continue
+        t0 = time.perf_counter()
+        sv = amgf.Solver(p.K, p.J, p.D, precision=prec)
+        tv_setup = time.perf_counter() - t0
+        if lrn:
+            sv.set_mlp(load_weights(WEIGHTS))
+        xv = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for k in range(2):
             xv.zero_()
-            sv.pcg_solve(bdev[0], xv)
-            d = xv - x_ref
-            yd = torch.empty_like(d)
-            yr = torch.empty_like(d)
-            s.matvec(d, yd)
-            s.matvec(x_ref, yr)
-            rel_a = float(torch.sqrt(torch.dot(d, yd) / torch.dot(x_ref, yr)))
-            variants[name] = {
-                "s_per_solve": e0.elapsed_time(e1) / nst * 1e-3, "pcg_iters": its,
-                "a_norm_rel_diff_vs_timed_solution": rel_a}
-            if learned:
-                variants[name]["mlp_fallbacks"] = fb
-            sv.close()
+            sv.pcg_solve(bdev[k % 3], xv)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its, fb, rr = [], 0, []
+        nst = max(3, min(args.steps, 10))
+        e0.record(stream)
+        for k in range(nst):
+            xv.zero_()
+            stv = sv.pcg_solve(bdev[k % 3], xv, stream=stream)
+            its.append(stv.iters)
+            fb += stv.mlp_fallback
+            rr.append(stv.rel_res_l2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        xv.zero_()
+        sv.pcg_solve(bdev[0], xv)
+        ent = {"workload": workload_name(args, prec, lrn), "s_per_solve": e0.elapsed_time(e1) / nst * 1e-3,
+               "steps": nst, "pcg_iters": its, "rel_res_l2": rr, "setup_s": round(tv_setup, 3),
+               "a_norm_rel_diff_vs_timed_solution": a_norm_rel(xv)}
+        if lrn:
+            ent["mlp_fallbacks"] = fb
+        if prec > 0:
+            ent["roofline"] = roofline_of(sv, 2, "fine", prec, hbm_peak, peak_kind, sm_count, sm_mhz,
+                                          "bsr3_mixed_kernel<POST>: fine-level l1-Jacobi sweep "
+                                          f"({PRECISIONS[prec]}, FP64 contact term)")
+            if sv.info.nlevels >= 3:
+                ent["roofline_coarse"] = roofline_of(sv, 3, "level1", prec, hbm_peak, peak_kind, sm_count, sm_mhz,
+                                                     f"csr_kernel<POST>: level-1 l1-Jacobi sweep ({PRECISIONS[prec]})")
+        variants[name] = ent
+        sv.close()
+    if variants:
         # FP64 rounding floor of the A-norm comparison: the same solve started 1e-10 |b| away
         # from zero.  Two solves equal in exact arithmetic differ by about this much, because the
         # true residual stalls near u |A| |x| in the contact rows (entries up to D_max).
         x2 = (1e-10 * bdev[0].abs()).contiguous()
         s.pcg_solve(bdev[0], x2)
-        d = x2 - x_ref
-        yd = torch.empty_like(d)
-        yr = torch.empty_like(d)
-        s.matvec(d, yd)
-        s.matvec(x_ref, yr)
-        floor = float(torch.sqrt(torch.dot(d, yd) / torch.dot(x_ref, yr)))
-
-    # dominant kernel: the fine-level l1-Jacobi post-smoother (one pass over the fine operator with
-    # the fused smoother epilogue), timed alone with CUDA events.  In FP64 the pass is bound by the
-    # FP64 pipe (2 FMA/clk/SM on this part), in the FP32 V-cycle by HBM bandwidth.
-    which = 2 if s.info.n and args.precision else 1
-    kms, kbytes = s.time_kernel(which, warmup=5, reps=50)
-    hbm_peak, peak_kind = peaks()
-    gbs = kbytes / (kms * 1e-3) / 1e9
-    nnz0 = int(s.info.level_nnz[0])
-    kflops = 2.0 * nnz0 + 4.0 * n          # 2 per nonzero, 4 per row (b - s, * w, + x, + add)
-    tflops = kflops / (kms * 1e-3) / 1e12
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
-            tr = json.load(f)
-        ent = tr.get(f"{args.config}:precision{args.precision}", {})
-        if ent.get("kernel_source_sha") == kernel_source_sha(args.precision):
-            traffic = ent.get("dram_bytes_per_launch")
-    except Exception:
-        pass
-    if args.precision == 0:
-        fp64_peak = fp64_peak_tflops()
-        roofline = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                    "frac": round(tflops / fp64_peak, 4), "traffic": traffic,
-                    "kernel": "bsr3_kernel<4,POST,0>: fine-level FP64 l1-Jacobi sweep over A (3x3 node blocks)",
-                    "flops_per_launch": kflops, "bytes_per_launch": kbytes, "ms_per_launch": kms,
-                    "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
-                    "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
-    else:
-        roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                    "frac": round(gbs / hbm_peak, 4), "traffic": traffic,
-                    "kernel": "bsr3_mixed_kernel<POST>: fine-level FP32 l1-Jacobi sweep (K blocks + FP64 contact term)",
-                    "bytes_per_launch": kbytes, "ms_per_launch": kms, "peak_kind": f"{peak_kind} (burst)"}
+        floor = a_norm_rel(x2)
+    nlev, opc, nc = int(info.nlevels), float(info.op_complexity), int(info.nc)
+    s.close()
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            est, sec_iter, t_orc_setup = cpu_oracle_sample(p, rhs, float(np.mean(iters)), args.cpu_iters)
-            cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                   "sample": f"{args.cpu_iters} oracle PCG iterations on the {args.config} system (setup "
-                             f"excluded, {t_orc_setup:.1f}s), {sec_iter * 1e3:.1f} ms/iteration scaled by the "
-                             f"GPU solve's mean {np.mean(iters):.1f} iterations"}
+            del bdev, x, x_ref
+            cpu = cpu_oracle_baseline(p, rhs)
         value = ms * 1e-3
         line = {
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32" + ("+bf16" if args.precision >= 2 else ""),
+            "vs_baseline": None,
+            "dtype": "f64" if args.precision == 0 else "f64+f32" + ("+bf16" if args.precision >= 2 else ""),
             "data": "synthetic",
-            "config": {"workload": workload_name(args),
-                       "precision": ["fp64", "fp32 V-cycle", "fp32 V-cycle, bf16 fine K",
-                                     "fp32 V-cycle, bf16 storage of all V-cycle matrices"][args.precision],
-                       "smoother": "l1-Jacobi, learned theta (MLP)" if weights is not None else "l1-Jacobi, theta = 1",
-                       "n": n, "m": p.m, "nc": int(info.nc), "levels": int(info.nlevels),
-                       "op_complexity": round(float(info.op_complexity), 4), "rtol": 1e-8,
-                       "stop": "sqrt(r^T z / r0^T z0)", "pcg_iters": iters,
-                       "l2": "working set larger than L2 (no flush)", "setup_s": round(t_setup, 3),
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "mlp_fallbacks": fallbacks,
-                       "aggregate_solves_per_s": world / (ms * 1e-3)},
+            "config": shared_config(args, p, args.precision, learned),
+            "solve": {"nc": nc, "levels": nlev, "op_complexity": round(opc, 4), "pcg_iters": iters,
+                      "rel_res_l2": relres, "setup_s": round(t_setup, 3), "mlp_fallbacks": fallbacks,
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                      "aggregate_solves_per_s": world / (ms * 1e-3)},
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * n * 8, "d2h_bytes_per_step": n * 8},
             "gpu_launches": int(launches),
             "roofline": roofline,
             "clocks": clocks,
         }
+        if roofline_coarse:
+            line["roofline_coarse"] = roofline_coarse
         if variants:
             line["variants"] = variants
             line["a_norm_rounding_floor"] = floor
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    s.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
 
-def fp64_peak_tflops():
-    """FP64 FMA pipe: 2 FMA per clock per SM on this part (nominal 1.25 TFLOP/s), 152 SMs, 2.07 GHz."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
-    except Exception:
-        mhz = 2070.0
-    return 152 * 2 * 2 * mhz * 1e6 / 1e12
-
-
-def kernel_source_sha(precision: int = 0):
-    """Hash of the source the roofline kernel of this precision is built from: the fine-level
-    FP64 BSR3 kernel (precision 0) or the mixed one (1-3), with the host code that lays its
-    operator out.  DRAM traffic stored in profiles/roofline_traffic.json is used only while
+def kernel_source_sha(kind: str = "fine", precision: int = 0):
+    """Hash of the source a roofline kernel is built from: the fine-level FP64 BSR3 kernel
+    (kind "fine", precision 0) or the mixed one (precision 1-3) with the host code that lays its
+    operator out, or the CSR level kernel with the host setup that builds the coarse levels
+    (kind "level1").  DRAM traffic stored in profiles/roofline_traffic.json is used only while
     this hash is unchanged."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2505_18576_gb300", "csrc")
     k = open(os.path.join(csrc, "kernels.cuh")).read()
+    a = open(os.path.join(csrc, "amgf.cu")).read()
+    c = open(os.path.join(csrc, "setup.cpp")).read()
+    if kind == "level1":
+        i = k.index("template <typename T, int K, int MODE, bool DOT, typename VT = T, int U = 4>")
+        h.update(k[i:k.index("// Fine-level operator in 3x3 node blocks", i)].encode())
+        i = a.index("static int lanes_for(")
+        h.update(a[i:a.index("static int grid_for(", i)].encode())
+        i = a.index("static int upload_csr(")
+        h.update(a[i:a.index("static void fill_info(", i)].encode())
+        h.update(c.encode())
+        return h.hexdigest()[:12]
     mid = k.index("// Fine level of the FP32 V-cycle")
     if precision == 0:
         h.update(k[k.index("struct BsrArgs {"):mid].encode())
     else:
         i = k.index("bsr3_mixed_kernel(Bsr3MixedArgs<VT> a) {")
         h.update(k[mid:k.index("\n}\n", i) + 3].encode())
-        a = open(os.path.join(csrc, "amgf.cu")).read()
         i = a.index("// fine-level K in 3x3 blocks")
         h.update(a[i:a.index("// contact term J^T D J over all rows", i)].encode())
-    c = open(os.path.join(csrc, "setup.cpp")).read()
     i = c.index("bool build_bsr3(")
     h.update(c[i:c.index("\nint validate_csr(", i)].encode())
     return h.hexdigest()[:12]
@@ -439,24 +537,26 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="amgf", choices=["amgf", "reference"])
-    ap.add_argument("--config", default="c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="c160", choices=sorted(WORKLOADS))
     ap.add_argument("--curvature", type=float, default=0.0,
                     help="contact rows along the normals of a curved interface (0: z-only node-to-node rows)")
-    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle PCG iterations timed for cpu_baseline")
-    ap.add_argument("--ref-iters", type=int, default=4, help="oracle PCG iterations per reference step")
+    ap.add_argument("--ref-iters", type=int, default=2, help="oracle PCG iterations per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
                     help="V-cycle precision of the timed solve: 0 FP64, 1 FP32, 2 FP32 with BF16 fine-level K, "
                          "3 FP32 arithmetic with BF16 storage of every V-cycle matrix")
-    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision variant timings")
-    ap.add_argument("--variants", default="all",
-                    help="comma list of variants to time (fp64, fp32_vcycle, fp32_vcycle_bf16_K, "
-                         "fp32_vcycle_bf16_all, fp32_vcycle_bf16_K_learned, fp32_vcycle_bf16_all_learned) or 'all'")
+    ap.add_argument("--variants", default=DEFAULT_VARIANTS,
+                    help="comma list of variants to time besides the main line (" + ", ".join(VARIANTS) +
+                         "), 'all' or 'none'")
     ap.add_argument("--weights", default=None,
                     help="learned smoother weights (.npz) for the timed solve; 'default' = the packaged c64 weights")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the PCG kernels directly instead of one CUDA graph (for per-kernel profiling)")
     args = ap.parse_args()
+    if args.variants not in ("all", "none"):
+        for v in args.variants.split(","):
+            if v not in VARIANTS:
+                ap.error(f"unknown variant {v}")
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

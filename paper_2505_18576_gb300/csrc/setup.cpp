@@ -399,9 +399,17 @@ bool cholesky(std::vector<double>& a, int64_t n) {
 // Inverse of an SPD matrix from its Cholesky factor: L L^T X = I solved for 8 columns of I at
 // a time, so that the inner loops run across the 8 right-hand sides (vector work, no
 // reductions); on Arm Neoverse cores 1.9x faster than column-by-column substitution.
+void spd_inverse_factored(const std::vector<double>& L, int64_t n, std::vector<double>& inv);
+
 bool spd_inverse(const std::vector<double>& a, int64_t n, std::vector<double>& inv) {
   std::vector<double> L(a);
   if (!cholesky(L, n)) return false;
+  spd_inverse_factored(L, n, inv);
+  return true;
+}
+
+// The same inverse from a Cholesky factor L (lower, row-major) that cholesky() already computed.
+void spd_inverse_factored(const std::vector<double>& L, int64_t n, std::vector<double>& inv) {
   inv.assign(n * n, 0.0);
   constexpr int64_t R = 8;
   const int64_t nbat = (n + R - 1) / R;
@@ -438,7 +446,6 @@ bool spd_inverse(const std::vector<double>& a, int64_t n, std::vector<double>& i
       const double s = 0.5 * (inv[i * n + j] + inv[j * n + i]);
       inv[i * n + j] = inv[j * n + i] = s;
     }
-  return true;
 }
 
 // C = A * B (n x n, row-major), C = alpha * A * B + beta * C
@@ -572,9 +579,11 @@ int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<dou
     for (int64_t k = 1; k < N; k += 2) {
       std::vector<double> r = A[k];
       std::vector<double> inv;
-      if (!cholesky(r, nb) || !spd_inverse(A[k], nb, inv)) {
+      if (!cholesky(r, nb)) {
 #pragma omp critical
         spd = false;
+      } else {
+        spd_inverse_factored(r, nb, inv);
       }
       R[k].swap(r);
       Ainv[k].swap(inv);
@@ -1290,10 +1299,11 @@ int build_filter(const HCSR& S, const amgf_csr* J, const amgf_options& o, Filter
     }
     std::vector<double> inv;
     Rprev = Dcur;
-    if (!cholesky(Rprev, nb) || !spd_inverse(Dcur, nb, inv)) {
+    if (!cholesky(Rprev, nb)) {
       err = "filter matrix A_w is not SPD";
       return AMGF_ERR_NOT_SPD;
     }
+    spd_inverse_factored(Rprev, nb, inv);
     std::copy(inv.begin(), inv.end(), F.Dinv.begin() + i * bsz);
   }
   }

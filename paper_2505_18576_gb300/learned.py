@@ -17,6 +17,7 @@ systems, with theta = 1 (plain AMGF) as the fallback.
 from __future__ import annotations
 
 import json
+import os
 import time
 
 import numpy as np
@@ -207,6 +208,30 @@ def run_experiment(config: str = "c64", n_train: int = 30, n_eval: int = 10, ite
     return res
 
 
+def run_evaluation(weights_path: str, config: str = "c64", n_eval: int = 10, precision: int = 1,
+                   verbose: bool = True) -> dict:
+    """Held-out evaluation of stored weights (no training): the systems of run_experiment's
+    evaluation set (seeds 200.., spreads drawn in [1e2, 1e10]), theta = 1 against the weights."""
+    import hashlib
+
+    import contactgen as cg
+    w = load_weights(weights_path)
+    K = cg.stiffness(**{k: cg.CONFIGS[config][k] for k in ("nx", "ny", "nz")})
+    J = cg.contact_jacobian(**{k: cg.CONFIGS[config][k] for k in ("nx", "ny", "nz")})
+    eval_set = ip_like_barriers(J.nrows, n_eval, seed0=200, held_out=True)
+    _, b = cg.draw_D_b(0, J.nrows, K.nrows, -2.0, 8.0)
+    ev = evaluate(K, J, eval_set, b, w, precision=precision)
+    res = {"config": config, "weights": os.path.basename(weights_path),
+           "weights_sha256": hashlib.sha256(w.tobytes()).hexdigest(), "precision": precision,
+           "plain_iters_total": sum(e["plain_iters"] for e in ev),
+           "learned_iters_total": sum(e["learned_iters"] for e in ev),
+           "plain_s_total": sum(e["plain_s"] for e in ev), "learned_s_total": sum(e["learned_s"] for e in ev),
+           "fallbacks": sum(e["fallback"] for e in ev), "eval": ev}
+    if verbose:
+        print(json.dumps({k: v for k, v in res.items() if k != "eval"}), flush=True)
+    return res
+
+
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser(description="train the learned smoother weights and compare with theta = 1")
@@ -222,8 +247,12 @@ if __name__ == "__main__":
     ap.add_argument("--ip", action="store_true",
                     help="train and evaluate on the Newton systems of interior-point runs (ip.py) instead")
     ap.add_argument("--nx", type=int, default=64, help="elements per side for --ip")
+    ap.add_argument("--evaluate", default=None, metavar="WEIGHTS",
+                    help="evaluate stored weights (.npz) on the held-out systems without training")
     a = ap.parse_args()
-    if a.ip:
+    if a.evaluate:
+        r = run_evaluation(a.evaluate, a.config, a.eval, a.precision)
+    elif a.ip:
         r = run_ip_experiment(a.nx, a.iters, a.lr, a.seed, a.precision, out=a.out)
     else:
         r = run_experiment(a.config, a.train, a.eval, a.iters, a.lr, a.seed, a.precision, a.out)

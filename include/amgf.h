@@ -292,6 +292,25 @@ int amgf_export_matrix(amgf_handle h, int which, int level, int64_t* nrows, int6
 /* Host copy of I_c (length nc, ascending DOF indices). */
 int amgf_export_contact_set(amgf_handle h, int64_t* ic);
 
+/* One launch of a PCG iteration, as recorded by amgf_profile_iteration. */
+typedef struct {
+  char op[64];    /* what the launch computes, e.g. "x + W (b - A x)" (the post-smoother) */
+  int level;      /* hierarchy level of its operator (-1: filter phases, PCG scalars) */
+  double ms;      /* CUDA-event time from the previous launch's end to this one's */
+  double bytes;   /* algorithmic bytes: stored values + indices at their precision, one read of
+                     every input vector (a gathered vector counted once), one write of every output */
+  double flops;   /* 2 per stored nonzero or dense-matrix entry applied (0 for vector kernels) */
+} amgf_launch_rec;
+
+/* Runs one PCG iteration (A p, the x/r update, one AMGF application, the p update and the stop
+ * test) on `stream` outside the captured graph, with a CUDA event after every kernel, and
+ * returns each launch's time, algorithmic bytes and flops in launch order (*count = number of
+ * launches; at most `cap` records are written).  Achieved bandwidth of a launch = bytes / ms.
+ * Meant for profiling after an amgf_pcg_solve on the same handle: it restarts PCG from the
+ * handle's current iterate (untimed) and runs one iteration of it; the next amgf_pcg_solve starts
+ * afresh.  Not part of the paper. */
+int amgf_profile_iteration(amgf_handle h, void* stream, amgf_launch_rec* recs, int cap, int* count);
+
 /* Time `reps` back-to-back launches of one kernel of the solve phase on `stream`
  * with CUDA events, after `warmup` untimed launches.  which: 0 = fine-level
  * A x (SpMV of level 0), 1 = fine-level FP64 post-smoother, 2 = fine-level post-smoother

@@ -22,7 +22,8 @@ __all__ = ["AmgfError", "Options", "Stats", "Info", "Solver", "load_library", "a
            "amgf_setup", "amgf_setup_host", "amgf_update_D", "amgf_apply", "amgf_vcycle", "amgf_matvec", "amgf_filter_solve",
            "amgf_filter_solve_noalloc", "amgf_filter_solve_host", "amgf_pcg_solve", "amgf_pcg_solve_host", "amgf_get_info", "amgf_export_matrix",
            "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy", "amgf_last_error", "EXPORTED",
-           "amgf_setup_bounds", "amgf_update_bounds", "amgf_update_D_fine", "amgf_apply_stages", "amgf_mlp_grad"]
+           "amgf_setup_bounds", "amgf_update_bounds", "amgf_update_D_fine", "amgf_apply_stages", "amgf_mlp_grad",
+           "amgf_profile_iteration"]
 
 EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_setup_bounds", "amgf_update_D",
             "amgf_update_bounds", "amgf_update_D_fine", "amgf_apply", "amgf_vcycle", "amgf_matvec",
@@ -30,7 +31,8 @@ EXPORTED = ["amgf_options_default", "amgf_setup", "amgf_setup_host", "amgf_setup
             "amgf_pcg_solve_host",
             "amgf_get_info",
             "amgf_export_matrix", "amgf_export_contact_set", "amgf_time_kernel", "amgf_destroy",
-            "amgf_last_error", "amgf_set_mlp", "amgf_mlp_train", "amgf_apply_stages", "amgf_mlp_grad"]
+            "amgf_last_error", "amgf_set_mlp", "amgf_mlp_train", "amgf_apply_stages", "amgf_mlp_grad",
+            "amgf_profile_iteration"]
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "NOT_SPD", 4: "BREAKDOWN", 5: "NOT_CONVERGED",
           6: "CUDA", 7: "OOM"}
@@ -62,6 +64,11 @@ class Stats(ctypes.Structure):
                 ("nlevels", ctypes.c_int), ("rel_res_precond", ctypes.c_double), ("rz0", ctypes.c_double),
                 ("t_solve_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("mlp_fallback", ctypes.c_int), ("rel_res_l2", ctypes.c_double), ("t_setup_s", ctypes.c_double)]
+
+
+class LaunchRec(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_char * 64), ("level", ctypes.c_int), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -112,6 +119,7 @@ def load_library(build_if_missing: bool = True):
         "amgf_set_mlp": [vp, vp, i64],
         "amgf_mlp_train": [vp, vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_uint64, vp],
         "amgf_mlp_grad": [vp, vp, vp, vp, vp],
+        "amgf_profile_iteration": [vp, vp, vp, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -360,6 +368,15 @@ def amgf_mlp_grad(h, params, r_all):
     return loss.value, g
 
 
+def amgf_profile_iteration(h, stream=None, cap: int = 4096):
+    """Per-launch records of one PCG iteration: list of dicts (op, level, ms, bytes, flops)."""
+    recs = (LaunchRec * cap)()
+    n = ctypes.c_int()
+    _check(load_library().amgf_profile_iteration(h, _stream(stream), recs, cap, ctypes.byref(n)))
+    return [{"op": r.op.decode(), "level": r.level, "ms": r.ms, "bytes": r.bytes, "flops": r.flops}
+            for r in recs[:min(n.value, cap)]]
+
+
 def amgf_destroy(h):
     if h:
         load_library().amgf_destroy(h)
@@ -405,6 +422,9 @@ class Solver:
 
     def mlp_grad(self, params, r_all):
         return amgf_mlp_grad(self.h, params, r_all)
+
+    def profile_iteration(self, stream=None):
+        return amgf_profile_iteration(self.h, stream)
 
     def vcycle(self, r, x, stream=None):
         amgf_vcycle(self.h, r, x, self.n, stream)

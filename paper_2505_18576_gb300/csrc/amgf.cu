@@ -52,6 +52,8 @@ static int fail(int code, const std::string& msg) {
 
 struct DCSR {
   int64_t nrows = 0, ncols = 0, nnz = 0;
+  int level = -1;   // hierarchy level (per-launch records of amgf_profile_iteration)
+  char role = 'A';  // 'A' level operator, 'P' interpolation, 'R' restriction, 'S' A[:, I_c] rows
   int64_t* rp = nullptr;
   int32_t* ci = nullptr;
   double* v = nullptr;
@@ -66,6 +68,8 @@ struct DCSR {
 
 struct DCSRf {  // FP32 (or BF16) values: V-cycle levels of the mixed-precision solve
   int64_t nrows = 0, ncols = 0, nnz = 0;
+  int level = -1;
+  char role = 'A';
   int64_t* rp = nullptr;
   int32_t* ci = nullptr;
   float* v = nullptr;
@@ -174,6 +178,14 @@ struct Ctx {
   size_t filter_smem = 0;
   int64_t launches = 0;       // kernels enqueued since the counter was last read
   int64_t init_launches = 0, body_launches = 0;
+  // per-launch records (amgf_profile_iteration): an event after every launch
+  struct ProfRec {
+    std::string op;
+    int level;
+    double bytes, flops;
+    cudaEvent_t ev;
+  };
+  std::vector<ProfRec>* prof = nullptr;
 
   ~Ctx() { release(); }
   void release_graph() {
@@ -228,6 +240,53 @@ struct Ctx {
 // ---------------------------------------------------------------------------------------
 // launch helpers
 
+// Counts one launch and, while profiling, records an event after it with the launch's
+// algorithmic bytes (values + indices at the stored precision, one read of every input vector,
+// one write of every output) and flops.
+static void counted(Ctx& c, const char* op, int level, double bytes, double flops = 0.0) {
+  c.launches++;
+  if (!c.prof) return;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, c.s);
+  c.prof->push_back({std::string(op), level, bytes, flops, e});
+}
+
+static const char* mode_name(int mode) {
+  switch (mode) {
+    case M_SPMV: return "A x";
+    case M_SPMV_ADD: return "y += A x";
+    case M_RESID: return "b - A x";
+    case M_RESID_W: return "b - A x, W (b - A x)";
+    case M_POST: return "x + W (b - A x)";
+    default: return "A x, W A x";
+  }
+}
+
+static const char* op_label(char role, int mode) {
+  switch (role) {
+    case 'P': return "prolongation x += P e";
+    case 'R': return mode == M_SPMV_W ? "restriction R r, W R r" : "restriction R r";
+    case 'S': return "r2 = r1 - A P w (rows touching I_c)";
+    default: return mode_name(mode);
+  }
+}
+
+// vector bytes per output row of a row-kernel epilogue (e: element size of the vectors)
+template <typename A>
+static double epilogue_bytes(int mode, const A& a, double e) {
+  double b = 0.0;
+  if (mode == M_SPMV) b = e;
+  else if (mode == M_SPMV_ADD) b = 2 * e;
+  else if (mode == M_RESID) b = 2 * e;
+  else if (mode == M_RESID_W) b = 3 * e + (a.y2 ? e : 0.0);
+  else if (mode == M_POST) b = 3 * e + (a.add ? 8.0 : 0.0);
+  else b = 2 * e + (a.y2 ? e : 0.0);
+  if (a.yf) b += 4.0;
+  if (a.y2f) b += 4.0;
+  return b;
+}
+
 // Lanes per row.  On a large level FP64 issue bounds the pass (~2 FMA/clk/SM on this part):
 // (ceil(len/K) + log2 K) K / 32 FP64 warp instructions per row is smallest for small K, and
 // K = 4 still reads whole 32-byte sectors of values.  A small level cannot fill the GPU with
@@ -281,7 +340,6 @@ template <int MODE>
 static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nullptr, double* result = nullptr) {
   a.rp = A.rp; a.ci = A.ci; a.v = A.v; a.nrows = A.nrows;
   if (A.nrows == 0) return;
-  c.launches++;
   if (A.bsr && !a.rows) {
     BsrArgs b{};
     b.soff = A.soff; b.bci = A.bci; b.v = A.bv; b.nbrows = A.nbrows; b.nslices = A.nslices;
@@ -294,6 +352,11 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
     } else {
       bsr3_kernel<MODE, false><<<grid, TPB, 0, c.s>>>(b);
     }
+    // 9 FP64 values + one block column per stored block, slice offsets, x gathered once, epilogue
+    counted(c, MODE == M_SPMV && result ? "A p, p^T A p" : op_label(A.role, MODE), A.level,
+            (double)A.nblocks * 76.0 + (double)(A.nslices + 1) * 8.0 + 8.0 * A.ncols +
+                A.nrows * (epilogue_bytes(MODE, a, 8.0) + (result ? 8.0 : 0.0)),
+            2.0 * A.nnz);
     return;
   }
   const int grid = grid_for(c, A.nrows, A.K);
@@ -303,14 +366,20 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
   } else {
     launch_csr_k<MODE, false>(A.K, grid, c.s, a);
   }
+  counted(c, op_label(A.role, MODE), A.level,
+          (double)A.nnz * 12.0 + (double)(A.nrows + 1) * 8.0 + 8.0 * A.ncols +
+              A.nrows * (epilogue_bytes(MODE, a, 8.0) + (a.rows ? 8.0 : 0.0) + (result ? 8.0 : 0.0)),
+          2.0 * A.nnz);
 }
 
 template <int MODE>
 static void launch_csr_f(Ctx& c, const DCSRf& A, CsrArgsT<float> a) {
   a.rp = A.rp; a.ci = A.ci; a.v = A.v; a.nrows = A.nrows;
   if (A.nrows == 0) return;
-  c.launches++;
   const int grid = grid_for(c, A.nrows, A.K);
+  const double vb = A.vb ? 2.0 : 4.0;
+  const double bytes = (double)A.nnz * (vb + 4.0) + (double)(A.nrows + 1) * 8.0 + 4.0 * A.ncols +
+                       A.nrows * epilogue_bytes(MODE, a, 4.0);
   if (A.vb) {
     CsrArgsT<float, __nv_bfloat16> b{};
     b.rp = a.rp; b.ci = a.ci; b.v = A.vb; b.nrows = a.nrows; b.rows = a.rows;
@@ -318,28 +387,30 @@ static void launch_csr_f(Ctx& c, const DCSRf& A, CsrArgsT<float> a) {
     b.yf = a.yf; b.y2f = a.y2f;
     if (A.U == 8) {
       csr_kernel<float, 32, MODE, false, __nv_bfloat16, 8><<<grid, TPB, 0, c.s>>>(b);
-      return;
+    } else {
+      switch (A.K) {
+        case 32: csr_kernel<float, 32, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
+        case 16: csr_kernel<float, 16, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
+        case 8: csr_kernel<float, 8, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
+        case 4: csr_kernel<float, 4, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
+        default: csr_kernel<float, 2, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
+      }
     }
-    switch (A.K) {
-      case 32: csr_kernel<float, 32, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
-      case 16: csr_kernel<float, 16, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
-      case 8: csr_kernel<float, 8, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
-      case 4: csr_kernel<float, 4, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
-      default: csr_kernel<float, 2, MODE, false, __nv_bfloat16><<<grid, TPB, 0, c.s>>>(b); break;
-    }
+    counted(c, op_label(A.role, MODE), A.level, bytes, 2.0 * A.nnz);
     return;
   }
   if (A.U == 8) {
     csr_kernel<float, 32, MODE, false, float, 8><<<grid, TPB, 0, c.s>>>(a);
-    return;
+  } else {
+    switch (A.K) {
+      case 32: csr_kernel<float, 32, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+      case 16: csr_kernel<float, 16, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+      case 8: csr_kernel<float, 8, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+      case 4: csr_kernel<float, 4, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+      default: csr_kernel<float, 2, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
+    }
   }
-  switch (A.K) {
-    case 32: csr_kernel<float, 32, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
-    case 16: csr_kernel<float, 16, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
-    case 8: csr_kernel<float, 8, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
-    case 4: csr_kernel<float, 4, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
-    default: csr_kernel<float, 2, MODE, false><<<grid, TPB, 0, c.s>>>(a); break;
-  }
+  counted(c, op_label(A.role, MODE), A.level, bytes, 2.0 * A.nnz);
 }
 
 // fine level of the FP32 V-cycle (K blocks + FP64 contact term)
@@ -347,7 +418,6 @@ template <int MODE>
 static void launch_fine_mixed(Ctx& c, const float* x, const float* b, const float* winv, const double* add,
                               float* y32, double* y64, const double* dotv, double* result) {
   const int grid = grid_for(c, c.k_nslices, 32);  // one warp per slice
-  c.launches++;
   auto fill = [&](auto& a) {
     a.soff = c.k_soff; a.bci = c.k_bci; a.nbrows = c.k_nbrows; a.nslices = c.k_nslices;
     a.crp = c.c_rp; a.cci = c.c_ci; a.cv = c.c_v;
@@ -367,6 +437,14 @@ static void launch_fine_mixed(Ctx& c, const float* x, const float* b, const floa
     if (result) bsr3_mixed_kernel<float, MODE, true><<<grid, TPB, 0, c.s>>>(a);
     else bsr3_mixed_kernel<float, MODE, false><<<grid, TPB, 0, c.s>>>(a);
   }
+  // K blocks (9 values + column), slice offsets, contact term (row pointers, 4 + 8 B per entry),
+  // x gathered once, epilogue vectors
+  const double vb = c.k_bf16 ? 2.0 : 4.0, n = (double)c.n;
+  const double epi = MODE == M_RESID ? 8.0 : 16.0 + (add ? 8.0 : 0.0) + (result ? 8.0 : 0.0);
+  counted(c, MODE == M_RESID ? "fine K blocks + FP64 contact: b - A x" : "fine K blocks + FP64 contact: x + W (b - A x)",
+          0, (double)c.k_nblocks * (9.0 * vb + 4.0) + (double)(c.k_nslices + 1) * 8.0 + (n + 1) * 4.0 +
+                 (double)c.c_nnz * 12.0 + 4.0 * n + n * epi,
+          2.0 * (double)c.L[0].A.nnz);
 }
 
 // coarsest-level solve: one warp per row of the dense inverse
@@ -398,7 +476,7 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
     // pre-smoothing from zero: x = W r (already in lv.x); residual r - A x
     if (cheb) {
       cheb_init_kernel<double><<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.x, lv.d, cf.inv_c);
-      c.launches++;
+      counted(c, "Chebyshev first step", l, 24.0 * lv.n);
     }
     CsrArgs a{};
     a.x = lv.x; a.b = rhs_of(l); a.y = lv.res;
@@ -409,7 +487,7 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
                                                                            cf.a[s], cf.bc[s]);
       else
         axpy_w_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.x);
-      c.launches++;
+      counted(c, cheb ? "Chebyshev step" : "x += W r", l, (cheb ? 48.0 : 32.0) * lv.n);
       CsrArgs rr{};
       rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
       launch_csr<M_RESID>(c, lv.A, rr);
@@ -433,7 +511,8 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
       dense_gemv_kernel<<<1, DENSE_TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, add0, oc, dotv, dotres);
     else
       dense_rows_kernel<double><<<dense_grid(c), DENSE_ROWS_TPB, 0, c.s>>>(c.nL, c.coarse_inv, rc, oc);
-    c.launches++;
+    counted(c, "coarsest: dense inverse x rhs", lc, 8.0 * (double)c.nL * (double)c.nL + 16.0 * c.nL,
+            2.0 * (double)c.nL * (double)c.nL);
   }
   for (int l = nlev - 2; l >= 0; --l) {
     DLevel& lv = c.L[l];
@@ -464,7 +543,7 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
             if (dot) go(std::false_type{}, std::true_type{}); else go(std::false_type{}, std::false_type{});
           }
         }
-        c.launches++;
+        counted(c, "Chebyshev step", l, 48.0 * lv.n);
       }
       continue;
     }
@@ -473,7 +552,7 @@ static void enqueue_vcycle(Ctx& c, const double* rhs0, double* out0, const doubl
       rr.x = lv.x; rr.b = rhs_of(l); rr.y = lv.res;
       launch_csr<M_RESID>(c, lv.A, rr);
       axpy_w_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winv, lv.res, lv.x);
-      c.launches++;
+      counted(c, "x += W r", l, 32.0 * lv.n);
     }
     CsrArgs po{};
     po.x = lv.x; po.b = rhs_of(l); po.winv = lv.winv;
@@ -497,7 +576,7 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
     DLevel& lv = c.L[l];
     if (cheb) {
       cheb_init_kernel<float><<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.xf, lv.df, (float)cf.inv_c);
-      c.launches++;
+      counted(c, "Chebyshev first step", l, 12.0 * lv.n);
     }
     for (int s = 0; s < nu; ++s) {
       if (s > 0) {
@@ -506,7 +585,7 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
                                                                             (float)cf.a[s], (float)cf.bc[s]);
         else
           axpy_w_f32_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.xf);
-        c.launches++;
+        counted(c, cheb ? "Chebyshev step" : "x += W r", l, (cheb ? 24.0 : 16.0) * lv.n);
       }
       if (l == 0) {
         launch_fine_mixed<M_RESID>(c, lv.xf, lv.rhsf, nullptr, nullptr, lv.resf, nullptr, nullptr, nullptr);
@@ -527,7 +606,8 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
   }
   dense_rows_kernel<float><<<dense_grid(c), DENSE_ROWS_TPB, 0, c.s>>>(c.nL, c.coarse_inv_f, c.L[nlev - 1].rhsf,
                                                                        c.L[nlev - 1].outf);
-  c.launches++;
+  counted(c, "coarsest: dense inverse x rhs", nlev - 1, 4.0 * (double)c.nL * (double)c.nL + 8.0 * c.nL,
+          2.0 * (double)c.nL * (double)c.nL);
   for (int l = nlev - 2; l >= 0; --l) {
     DLevel& lv = c.L[l];
     CsrArgsT<float> pa{};
@@ -569,7 +649,7 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
                                                                            bj, nullptr, lv.outf, nullptr, nullptr,
                                                                            nullptr, nullptr);
         }
-        c.launches++;
+        counted(c, "Chebyshev step", l, 24.0 * lv.n);
       }
       continue;
     }
@@ -582,7 +662,7 @@ static void enqueue_vcycle_f32(Ctx& c, double* out0, const double* add0, const d
         launch_csr_f<M_RESID>(c, lv.Af, rr);
       }
       axpy_w_f32_kernel<<<vec_grid(c, lv.n), TPB, 0, c.s>>>(lv.n, lv.winvf, lv.resf, lv.xf);
-      c.launches++;
+      counted(c, "x += W r", l, 16.0 * lv.n);
     }
     if (l == 0) {
       launch_fine_mixed<M_POST>(c, lv.xf, lv.rhsf, lv.winvf, add0, nullptr, out0, dotv, dotres);
@@ -600,7 +680,7 @@ static void enqueue_scale_w0(Ctx& c, const double* r) {
   } else {
     scale_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.L[0].winv, r, c.L[0].x);
   }
-  c.launches++;
+  counted(c, c.mixed ? "W r (FP32 copies)" : "W r", 0, (c.mixed ? 24.0 : 24.0) * c.n);
 }
 
 // B rhs0 in the configured precision (see enqueue_vcycle / enqueue_vcycle_f32 for the entry state)
@@ -630,7 +710,8 @@ static void launch_sweep(Ctx& c, bool fwd, const double* M, const double* r, con
     cudaLaunchKernelEx(&cfg, filter_sweep_kernel<true>, fwd, M, (const int64_t*)c.fgidx, r, vdirect, zin, nc, nb, nblk, out);
   else
     cudaLaunchKernelEx(&cfg, filter_sweep_kernel<false>, fwd, M, (const int64_t*)c.fgidx, r, vdirect, zin, nc, nb, nblk, out);
-  c.launches++;
+  counted(c, fwd ? "filter: block LDL^T forward sweep" : "filter: block LDL^T backward sweep", -1,
+          8.0 * (double)(nblk - 1) * nb * nb + 16.0 * nb * nblk, 2.0 * (double)(nblk - 1) * nb * nb);
 }
 
 // out (factor order, length nblk*nb) = A_w^{-1} v with v gathered from r at gidx (or given
@@ -655,7 +736,15 @@ static void enqueue_filter_solve_into(Ctx& c, const double* r, const double* vdi
       } else {
         if (wide) go(filter_bcr_kernel<false, 32>); else go(filter_bcr_kernel<false, 8>);
       }
-      c.launches++;
+      // each task reads its one or two nb x nb matrices and input blocks and writes one block
+      double mats = 0.0, blks = 0.0;
+      for (int64_t k = t0; k < t0 + nt; ++k) {
+        const FilterTask& ft = c.F.tasks[k];
+        mats += (ft.m0 >= 0 && ft.in0 >= 0) + (ft.m1 >= 0 && ft.in1 >= 0);
+        blks += 1.0 + (ft.in0 >= 0) + (ft.in1 >= 0);
+      }
+      counted(c, q == 0 ? "filter: cyclic reduction phase (gathers P^T r1)" : "filter: cyclic reduction phase", -1,
+              8.0 * mats * nb * nb + 8.0 * blks * nb, 2.0 * mats * nb * nb);
     }
     return;
   }
@@ -664,7 +753,8 @@ static void enqueue_filter_solve_into(Ctx& c, const double* r, const double* vdi
   int g = (int)((rows * 32 + TPB - 1) / TPB);
   if (g > c.num_sms * 8) g = c.num_sms * 8;
   filter_diag_kernel<<<g, TPB, 0, c.s>>>(c.fDinv, y, z, nb, nblk);
-  c.launches++;
+  counted(c, "filter: block pivots", -1, 8.0 * (double)nblk * nb * nb + 16.0 * nb * nblk,
+          2.0 * (double)nblk * nb * nb);
   launch_sweep(c, false, c.fGT, nullptr, nullptr, z, out);
 }
 
@@ -706,7 +796,7 @@ static void enqueue_apply(Ctx& c, const double* r, double* z, double* dotres, co
     if (tap && tap->w)
       permute_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.F.nc, c.ficidx, nullptr, c.fw, tap->w);
     filter_scatter_kernel<<<vec_grid(c, c.F.nc), TPB, 0, c.s>>>(c.fgidx, c.fw, c.y1, c.F.nc);  // y2 = y1 + P w
-    c.launches++;
+    counted(c, "y2 = y1 + P w", 0, 32.0 * c.F.nc);
     CsrArgs sa{};                                                                              // r2 = r1 - A P w
     sa.rows = c.ftouch; sa.x = c.fw; sa.b = c.r1; sa.y = c.r1; sa.w2 = c.L[0].winv;
     if (c.mixed) { sa.yf = c.L[0].rhsf; sa.y2f = c.L[0].xf; } else { sa.y2 = c.L[0].x; }
@@ -725,10 +815,13 @@ static void enqueue_pcg_body(Ctx& c, int use_cond) {
   pcg_update_xr_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(
       c.st, c.p, c.q, c.x, c.r, c.L[0].winv, c.mixed ? nullptr : c.L[0].x, c.mixed ? c.L[0].rhsf : nullptr,
       c.mixed ? c.L[0].xf : nullptr, c.mixed ? c.z : nullptr, c.partial, c.counter, c.n);
+  // p, q, W read; x, r read and written; W r written (FP64, or FP32 r and W r plus z read)
+  counted(c, "PCG: x += alpha p, r -= alpha q, W r", 0, (c.mixed ? 72.0 : 64.0) * c.n);
   enqueue_apply(c, c.r, c.z, &c.st->rz_new);
   pcg_update_p_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.st, c.z, c.p, c.n);
+  counted(c, "PCG: p = z + beta p", 0, 24.0 * c.n);
   pcg_finalize_kernel<<<1, 1, 0, c.s>>>(c.st, c.cond, use_cond);
-  c.launches += 3;
+  counted(c, "PCG: scalars and stop test", -1, 0.0);
 }
 
 static void enqueue_pcg_init(Ctx& c) {
@@ -738,8 +831,9 @@ static void enqueue_pcg_init(Ctx& c) {
   launch_csr<M_RESID_W>(c, c.L[0].A, ra);               // r0 = b - A x0, W_0 r0
   enqueue_apply(c, c.r, c.z, &c.st->rz_new);             // z0 = M r0, rz_new = r0^T z0
   pcg_init_kernel<<<1, 1, 0, c.s>>>(c.st, c.o.maxit, c.o.rtol, c.mixed ? 1 : 0);
+  counted(c, "PCG: initial scalars", -1, 0.0);
   copy_kernel<<<vec_grid(c, c.n), TPB, 0, c.s>>>(c.n, c.z, c.p);  // p0 = z0
-  c.launches += 2;
+  counted(c, "PCG: p = z", 0, 16.0 * c.n);
 }
 
 static int build_graph(Ctx& c) {
@@ -1254,6 +1348,12 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       if (c.o.smoother == 1 && (st = c.alloc(&lv.df, lv.n))) return st;
     }
   }
+  for (int l = 0; l < nlev; ++l) {  // labels of the per-launch records
+    DLevel& lv = c.L[l];
+    lv.A.level = lv.P.level = lv.R.level = lv.Af.level = lv.Pf.level = lv.Rf.level = l;
+    lv.P.role = lv.Pf.role = 'P';
+    lv.R.role = lv.Rf.role = 'R';
+  }
   // learned-smoother inputs: features and l1 of every smoothed level
   {
     std::vector<std::vector<float>> feat;
@@ -1353,6 +1453,8 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
     if ((st = c.upload(&c.ficidx, fic.data(), c.F.nc))) return st;
     if ((st = c.upload(&c.ftouch, c.F.touch_rows.data(), (int64_t)c.F.touch_rows.size()))) return st;
     if ((st = upload_csr(c, c.F.Sc, c.fSc))) return st;
+    c.fSc.level = 0;
+    c.fSc.role = 'S';
     if ((st = c.alloc(&c.fy, tot))) return st;
     if ((st = c.alloc(&c.fz, tot))) return st;
     if ((st = c.alloc(&c.fw, tot))) return st;
@@ -1724,7 +1826,7 @@ static int solve_device(Ctx& c, amgf_stats* stats) {
     // kernels of the init part plus one body per executed loop trip (a body also runs once
     // when the initial residual already meets the stop test)
     const int64_t trips = s.iter > 0 ? s.iter : (c.o.use_graph ? 1 : 0);
-    stats->kernel_launches = c.init_launches + trips * c.body_launches;
+    stats->kernel_launches = c.init_launches + trips * c.body_launches + 3;  // + the true-residual check
     stats->rel_res_l2 = res2[1] > 0.0 ? std::sqrt(res2[0] / res2[1]) : 0.0;
     stats->t_setup_s = c.info.t_setup_s;
   }
@@ -1811,6 +1913,49 @@ int amgf_mlp_grad(amgf_handle h, const float* params, const double* r_all, float
   return mlp_grad_impl(h->c, params, r_all, grad, loss);
 }
 
+int amgf_profile_iteration(amgf_handle h, void* stream, amgf_launch_rec* recs, int cap, int* count) {
+  if (h && h->c.host_only) return fail(AMGF_ERR_INVALID_ARG, "host-only handle (amgf_setup_host)");
+  if (!h || !count || cap < 0 || (cap > 0 && !recs)) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
+  Ctx& c = h->c;
+  CK(cudaSetDevice(c.device));
+  int st = join_begin(c, stream);
+  if (st) return st;
+  // a fresh PCG start from the current x (r0 = b - A x0, z0 = M r0), so that the iteration
+  // below runs every kernel on live state (the vector kernels skip their work once the stop
+  // test has been met)
+  enqueue_pcg_init(c);
+  std::vector<Ctx::ProfRec> v;
+  cudaEvent_t e0 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventRecord(e0, c.s));
+  c.prof = &v;
+  enqueue_pcg_body(c, 0);
+  c.prof = nullptr;
+  const cudaError_t le = cudaGetLastError();
+  const cudaError_t se = cudaStreamSynchronize(c.s);
+  cudaEvent_t prev = e0;
+  for (size_t k = 0; k < v.size(); ++k) {
+    float ms = 0.f;
+    if (le == cudaSuccess && se == cudaSuccess) cudaEventElapsedTime(&ms, prev, v[k].ev);
+    if ((int)k < cap) {
+      amgf_launch_rec& r = recs[k];
+      std::memset(&r, 0, sizeof r);
+      std::snprintf(r.op, sizeof r.op, "%s", v[k].op.c_str());
+      r.level = v[k].level;
+      r.ms = ms;
+      r.bytes = v[k].bytes;
+      r.flops = v[k].flops;
+    }
+    prev = v[k].ev;
+  }
+  for (auto& r : v) cudaEventDestroy(r.ev);
+  cudaEventDestroy(e0);
+  if (le != cudaSuccess) return fail(AMGF_ERR_CUDA, std::string("profile: ") + cudaGetErrorString(le));
+  if (se != cudaSuccess) return fail(AMGF_ERR_CUDA, std::string("profile: ") + cudaGetErrorString(se));
+  *count = (int)v.size();
+  return join_end(c, stream);
+}
+
 int amgf_get_info(amgf_handle h, amgf_info* info) {
   if (!h || !info) return fail(AMGF_ERR_INVALID_ARG, "bad arguments");
   *info = h->c.info;
@@ -1890,10 +2035,11 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
     const double vb = c.mixed ? (l1.Af.vb ? 2.0 : 4.0) : 8.0, eb = c.mixed ? 4.0 : 8.0;
     const double nz1 = (double)(c.mixed ? l1.Af.nnz : l1.A.nnz), n1 = (double)l1.n;
     *bytes = nz1 * (vb + 4.0) + (n1 + 1.0) * 8.0 + 4.0 * eb * n1;
-  } else if (which == 2) {  // K blocks (4 or 2 bytes per value + index), contact CSR, 3 FP32 reads + FP64 write
+  } else if (which == 2) {  // K blocks (4 or 2 bytes per value + index), contact CSR (row pointers, 4 + 8 B
+                            // per entry), 3 FP32 reads + FP64 write
     const double vb = c.k_bf16 ? 2.0 : 4.0;
     *bytes = (double)c.k_nblocks * (9.0 * vb + 4.0) + (double)(c.k_nslices + 1) * 8.0 + (n + 1) * 4.0 +
-             3.0 * 4.0 * n + 8.0 * n;
+             (double)c.c_nnz * 12.0 + 3.0 * 4.0 * n + 8.0 * n;
   } else if (l0.A.bsr)  // 9 values + one block column index per stored block (padding excluded), slice offsets
     *bytes = (double)l0.A.nblocks * (9.0 * 8.0 + 4.0) + (double)(l0.A.nslices + 1) * 8.0 + vec_bytes;
   else

@@ -91,6 +91,10 @@ def test_c160_matvec_and_solves(c160):
               f"galerkin residual {gal:.2e}")
         assert st.status == 0 and st.converged == 1
         assert gal <= 1e-4
+        # guard of the measured iteration count (32-34 over seeds 0-2 in FP64, 32 with the
+        # BF16 fine-level K): the counts jump when the hierarchy crosses a step of the strength
+        # threshold, which doubles the solve time
+        assert st.iters <= 36
         xs[prec] = xh
         if prec == 0:
             x2 = (1e-10 * b.abs()).contiguous()

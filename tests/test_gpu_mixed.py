@@ -77,7 +77,7 @@ def test_mixed_pcg_against_fp64_oracle(case, precision):
     print(f"{name} precision {precision}: iters {st.iters} (fp64 oracle {ko}), A-norm diff {ea:.2e} "
           f"(bound {bound:.2e}, floor {floor:.2e})")
     assert st.status == 0 and st.converged == 1
-    assert st.iters <= 2 * ko + 5
+    assert st.iters <= ko + 2
     assert ea <= bound
     s.close()
 
@@ -97,8 +97,10 @@ def test_mixed_apply_close_to_fp64(case, precision):
     # FP32: the V-cycle's 1e-7 error, amplified by the filter step.  BF16 on every V-cycle
     # matrix: the V-cycle differs by ~2e-3, and the filter correction A_w^{-1} P^T (r - A y1)
     # responds to that error through contact rows with entries up to D_max, so the apply
-    # moves by up to ~10% while the preconditioner quality (PCG iterations, above) does not.
-    assert err <= (1e-3 if precision == 1 else 0.2)
+    # moves by a few percent (measured 1.6e-2 at 8x8x4, 7.8e-4 at 24x24x12) while the
+    # preconditioner quality (PCG iterations, above) does not; tests/test_gpu_stages.py checks
+    # every FP64 step of this apply with rounding-level bounds.
+    assert err <= (1e-3 if precision == 1 else 4e-2)
     s.close()
 
 

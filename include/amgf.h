@@ -100,6 +100,14 @@ typedef struct {
                              residual pass plus one vector update per degree.  Learned weights
                              (amgf_set_mlp) apply to smoother 0 only. */
   double cheby_lower;     /* lower end of the Chebyshev interval, in (0, 1) (0.3) */
+  int stage_rows;         /* BF16 V-cycle matrices (precision 3): rows per tile of the staged sweeps of
+                             the coarse levels whose rows hold at most 160 entries on average; a
+                             producer warp copies each tile's row pointers, indices, values and
+                             vectors into shared memory with bulk asynchronous copies while the
+                             other warps sweep the tiles before it (32; rounded up to whole passes
+                             of the CTA's row groups; 0: plain loads, csr_kernel, everywhere).
+                             Same results either way.  At most 4096. */
+  int stage_depth;        /* tiles in flight per CTA of the staged sweeps, 2..8 (2) */
 } amgf_options;
 
 typedef struct {
@@ -133,6 +141,7 @@ typedef struct {
   double t_assemble_s;       /* of which: assembling A */
   double t_hierarchy_s;      /*           the AMG hierarchy */
   double t_filter_s;         /*           I_c, ordering and the A_w factor */
+  int64_t staged_levels;     /* bit l set: the sweeps of level l run staged (amgf_options.stage_rows) */
 } amgf_info;
 
 typedef struct amgf_ctx* amgf_handle;

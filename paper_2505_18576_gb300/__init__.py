@@ -56,7 +56,8 @@ class Options(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("precision", ctypes.c_int), ("filter_algo", ctypes.c_int),
                 ("interp", ctypes.c_int), ("p_max", ctypes.c_int), ("update_in_place", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("cheby_lower", ctypes.c_double)]
+                ("smoother", ctypes.c_int), ("cheby_lower", ctypes.c_double),
+                ("stage_rows", ctypes.c_int), ("stage_depth", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -77,7 +78,8 @@ class Info(ctypes.Structure):
                 ("interp_nnz", ctypes.c_int64 * 32), ("filter_block", ctypes.c_int64),
                 ("filter_nblocks", ctypes.c_int64), ("op_complexity", ctypes.c_double),
                 ("t_setup_s", ctypes.c_double), ("t_assemble_s", ctypes.c_double),
-                ("t_hierarchy_s", ctypes.c_double), ("t_filter_s", ctypes.c_double)]
+                ("t_hierarchy_s", ctypes.c_double), ("t_filter_s", ctypes.c_double),
+                ("staged_levels", ctypes.c_int64)]
 
 
 _lib = None

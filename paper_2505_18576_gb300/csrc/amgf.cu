@@ -76,6 +76,10 @@ struct DCSRf {  // FP32 (or BF16) values: V-cycle levels of the mixed-precision 
   __nv_bfloat16* vb = nullptr;  // BF16 values instead of v (precision 3)
   int K = 4;
   int U = 4;                    // entries per lane and batch (8: long rows on a warp per row)
+  // staged sweeps (csr_staged_kernel) of a level operator; sg.ntiles == 0: csr_kernel
+  StageArgs sg{};
+  int sgrid = 0;
+  size_t ssmem = 0;
 };
 
 struct DLevel {
@@ -166,6 +170,7 @@ struct Ctx {
   double* partial = nullptr;
   unsigned* counter = nullptr;
   double* scratch_scalar = nullptr;
+  int* kerr = nullptr;  // set by a staged sweep whose wait gave up (checked after solves)
   PcgState* st = nullptr;
   PcgState* st_host = nullptr;  // pinned
   cudaGraph_t graph = nullptr;
@@ -203,6 +208,7 @@ struct Ctx {
     l1_d.clear();
     mlp_w = mlp_m = mlp_v = mlp_g = mlp_part = mlp_loss = nullptr;
     mlp_tw = mlp_ee = mlp_rr = nullptr;
+    kerr = nullptr;
     mlp_part_blocks = 0;
     mlp_loss_cap = 0;
   }
@@ -231,6 +237,22 @@ struct Ctx {
   template <class T>
   int upload(T** ptr, const T* host, int64_t count) {
     int st_ = alloc(ptr, count);
+    if (st_) return st_;
+    if (count > 0) CK(cudaMemcpy(*ptr, host, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
+    return AMGF_OK;
+  }
+  // count entries followed by `pad` zeros (the aligned segments of the staged sweeps may reach
+  // up to 15 entries past the end of an array)
+  template <class T>
+  int alloc_padded(T** ptr, int64_t count, int64_t pad) {
+    int st_ = alloc(ptr, count + pad);
+    if (st_) return st_;
+    CK(cudaMemset(*ptr, 0, (size_t)(count + pad) * sizeof(T)));
+    return AMGF_OK;
+  }
+  template <class T>
+  int upload_padded(T** ptr, const T* host, int64_t count, int64_t pad) {
+    int st_ = alloc_padded(ptr, count, pad);
     if (st_) return st_;
     if (count > 0) CK(cudaMemcpy(*ptr, host, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
     return AMGF_OK;
@@ -372,6 +394,27 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
           2.0 * A.nnz);
 }
 
+// entries per lane and batch of the staged sweeps
+constexpr int STAGE_U = 8;
+
+template <int MODE, typename VT>
+static const void* staged_fn(int K) {
+  switch (K) {
+    case 32: return (const void*)csr_staged_kernel<MODE, VT, 32, STAGE_U>;
+    case 16: return (const void*)csr_staged_kernel<MODE, VT, 16, STAGE_U>;
+    default: return (const void*)csr_staged_kernel<MODE, VT, 8, STAGE_U>;
+  }
+}
+
+template <int MODE, typename VT>
+static void launch_staged(Ctx& c, const DCSRf& A, const CsrArgsT<float, VT>& a) {
+  switch (A.K) {
+    case 32: csr_staged_kernel<MODE, VT, 32, STAGE_U><<<A.sgrid, STAGE_TPB, A.ssmem, c.s>>>(a, A.sg); break;
+    case 16: csr_staged_kernel<MODE, VT, 16, STAGE_U><<<A.sgrid, STAGE_TPB, A.ssmem, c.s>>>(a, A.sg); break;
+    default: csr_staged_kernel<MODE, VT, 8, STAGE_U><<<A.sgrid, STAGE_TPB, A.ssmem, c.s>>>(a, A.sg); break;
+  }
+}
+
 template <int MODE>
 static void launch_csr_f(Ctx& c, const DCSRf& A, CsrArgsT<float> a) {
   a.rp = A.rp; a.ci = A.ci; a.v = A.v; a.nrows = A.nrows;
@@ -380,11 +423,21 @@ static void launch_csr_f(Ctx& c, const DCSRf& A, CsrArgsT<float> a) {
   const double vb = A.vb ? 2.0 : 4.0;
   const double bytes = (double)A.nnz * (vb + 4.0) + (double)(A.nrows + 1) * 8.0 + 4.0 * A.ncols +
                        A.nrows * epilogue_bytes(MODE, a, 4.0);
+  // level operator sweeps with plain epilogues: staged tiles (csr_staged_kernel)
+  constexpr bool kStagedMode = MODE == M_RESID || MODE == M_POST;
+  const bool staged = kStagedMode && A.sg.ntiles > 0 && !a.rows && !a.add && !a.y2 && !a.yf && !a.y2f;
   if (A.vb) {
     CsrArgsT<float, __nv_bfloat16> b{};
     b.rp = a.rp; b.ci = a.ci; b.v = A.vb; b.nrows = a.nrows; b.rows = a.rows;
     b.x = a.x; b.b = a.b; b.winv = a.winv; b.w2 = a.w2; b.add = a.add; b.y = a.y; b.y2 = a.y2;
     b.yf = a.yf; b.y2f = a.y2f;
+    if constexpr (kStagedMode) {
+      if (staged) {
+        launch_staged<MODE, __nv_bfloat16>(c, A, b);
+        counted(c, op_label(A.role, MODE), A.level, bytes, 2.0 * A.nnz);
+        return;
+      }
+    }
     if (A.U == 8) {
       csr_kernel<float, 32, MODE, false, __nv_bfloat16, 8><<<grid, TPB, 0, c.s>>>(b);
     } else {
@@ -1007,15 +1060,16 @@ static int upload_csr(Ctx& c, const HCSR& h, DCSR& d) {
 static int upload_csr_f(Ctx& c, const HCSR& h, DCSRf& d) {
   d.nrows = h.nrows; d.ncols = h.ncols; d.nnz = h.nnz();
   int st;
-  if ((st = c.upload(&d.rp, h.rp.data(), h.nrows + 1))) return st;
-  if ((st = c.upload(&d.ci, h.ci.data(), d.nnz))) return st;
+  // padded for the 16-byte aligned segments of the staged sweeps
+  if ((st = c.upload_padded(&d.rp, h.rp.data(), h.nrows + 1, 2))) return st;
+  if ((st = c.upload_padded(&d.ci, h.ci.data(), d.nnz, 16))) return st;
   if (c.o.precision == 3) {  // BF16 storage, round to nearest even
     std::vector<__nv_bfloat16> v(d.nnz);
     for (int64_t k = 0; k < d.nnz; ++k) v[k] = __float2bfloat16_rn((float)h.v[k]);
-    if ((st = c.upload(&d.vb, v.data(), d.nnz))) return st;
+    if ((st = c.upload_padded(&d.vb, v.data(), d.nnz, 16))) return st;
   } else {
     std::vector<float> v(h.v.begin(), h.v.end());
-    if ((st = c.upload(&d.v, v.data(), d.nnz))) return st;
+    if ((st = c.upload_padded(&d.v, v.data(), d.nnz, 16))) return st;
   }
   const double avg = h.nrows ? (double)d.nnz / (double)h.nrows : 1.0;
   d.K = lanes_for_f32(h.nrows, avg, c.num_sms);
@@ -1023,6 +1077,74 @@ static int upload_csr_f(Ctx& c, const HCSR& h, DCSRf& d) {
   // lane and batch (sweep on GB300: 17-30% faster than 16 lanes with 4 entries)
   if (avg >= 300 && h.nrows < 500000) { d.K = 32; d.U = 8; }
   return AMGF_OK;
+}
+
+constexpr int STAGE_SMEM_MAX = 200 * 1024;  // dynamic shared memory of a staged CTA at most
+
+template <typename VT>
+static int plan_staging_t(Ctx& c, DCSRf& d, StageArgs g) {
+  // the POST instance stages three vectors, RESID one: size both by POST
+  size_t smem = stage_smem_bytes<M_POST, VT>(g);
+  while (g.depth > 2 && smem > (size_t)STAGE_SMEM_MAX) {
+    --g.depth;
+    smem = stage_smem_bytes<M_POST, VT>(g);
+  }
+  if (smem > (size_t)STAGE_SMEM_MAX) return AMGF_OK;  // tiles too long: csr_kernel
+  // one kernel instance serves every level with the same K and value type, so its limit is the
+  // largest any level may ask for, not this level's size
+  const void* fr = staged_fn<M_RESID, VT>(d.K);
+  const void* fp = staged_fn<M_POST, VT>(d.K);
+  CK(cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_SMEM_MAX));
+  CK(cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGE_SMEM_MAX));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fp, STAGE_TPB, smem));
+  if (per_sm < 1) return AMGF_OK;
+  const int64_t want = (int64_t)per_sm * c.num_sms;
+  d.sg = g;
+  d.ssmem = smem;
+  d.sgrid = (int)(g.ntiles < want ? g.ntiles : want);
+  return AMGF_OK;
+}
+
+// Staged sweeps for a level operator of the FP32 V-cycle with BF16 values: tiles of o.stage_rows
+// rows (rounded up to whole passes of the CTA's row groups), o.stage_depth tiles in flight per
+// CTA, one persistent CTA per resident slot.  Only where they were measured faster on GB300 (the
+// level-1 sweeps of c64-c160, rows of 96-135 entries: 7-16%): BF16 values and at most
+// STAGE_MAX_AVG entries per row on average.  Longer rows make a tile take so much shared memory
+// that too few CTAs stay resident to keep the gathers of x in flight (c160 level 3: 2x slower);
+// FP32 values were slower at every level.  Other levels keep csr_kernel.
+constexpr double STAGE_MAX_AVG = 160.0;
+static int plan_staging(Ctx& c, const HCSR& h, DCSRf& d) {
+  d.sg = StageArgs{};
+  d.sgrid = 0;
+  d.ssmem = 0;
+  if (c.o.stage_rows <= 0 || d.nrows == 0 || !d.vb || d.K < 8 || d.U != 4) return AMGF_OK;
+  if ((double)d.nnz / (double)d.nrows > STAGE_MAX_AVG) return AMGF_OK;
+  if (!c.kerr) {
+    int st;
+    if ((st = c.alloc_padded(&c.kerr, 1, 0))) return st;
+  }
+  const int G = STAGE_NW * (32 / d.K);
+  const int64_t R = ((int64_t)c.o.stage_rows + G - 1) / G * G;
+  const int64_t ntiles = (d.nrows + R - 1) / R;
+  if (ntiles < c.num_sms) return AMGF_OK;
+  int64_t cap = 0;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const int64_t r0 = t * R, r1 = r0 + R < d.nrows ? r0 + R : d.nrows;
+    const int64_t ka = h.rp[r0] & ~(int64_t)7;
+    const int64_t kn = (h.rp[r1] - ka + 7) & ~(int64_t)7;
+    cap = kn > cap ? kn : cap;
+  }
+  if (cap > (int64_t)1 << 20) return AMGF_OK;
+  StageArgs g{};
+  g.ntiles = ntiles;
+  g.rows = (int)R;
+  g.depth = c.o.stage_depth < 2 ? 2 : (c.o.stage_depth > STAGE_MAX_DEPTH ? STAGE_MAX_DEPTH : c.o.stage_depth);
+  g.cap = (int)(cap < 8 ? 8 : cap);
+  g.rp_cap = (int)R + 4;
+  g.vec_cap = (int)((R + 6) & ~(int64_t)3);
+  g.err = c.kerr;
+  return plan_staging_t<__nv_bfloat16>(c, d, g);
 }
 
 static void fill_info(Ctx& c) {
@@ -1040,6 +1162,8 @@ static void fill_info(Ctx& c) {
   in.op_complexity = tot / (double)c.H.A[0].nnz();
   in.filter_block = c.F.nb;
   in.filter_nblocks = c.F.nblk;
+  for (size_t l = 0; l < c.L.size() && l < 63; ++l)
+    if (c.L[l].Af.sg.ntiles > 0) in.staged_levels |= (int64_t)1 << l;
 }
 
 // dst[idx[k]] = val[k] on the device (temporary buffers, synchronous)
@@ -1291,6 +1415,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   if (c.host_only) return AMGF_OK;
   // ---- device upload
   c.release_device();
+  c.info.staged_levels = 0;
   c.bsr0 = BSR3();
   const int nlev = c.H.nlev();
   c.L.assign(nlev, DLevel());
@@ -1340,9 +1465,12 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
         if ((st = upload_csr_f(c, c.H.R[l], lv.Rf))) return st;
       }
       std::vector<float> wf(w.begin(), w.end());
-      if ((st = c.upload(&lv.winvf, wf.data(), lv.n))) return st;
-      if ((st = c.alloc(&lv.rhsf, lv.n))) return st;
-      if ((st = c.alloc(&lv.xf, lv.n))) return st;
+      // W, b and x of a level are staged in 16-byte segments by the staged sweeps
+      if ((st = c.upload_padded(&lv.winvf, wf.data(), lv.n, 8))) return st;
+      if ((st = c.alloc_padded(&lv.rhsf, lv.n, 8))) return st;
+      if ((st = c.alloc_padded(&lv.xf, lv.n, 8))) return st;
+      if (l > 0 && (st = plan_staging(c, c.H.A[l], lv.Af))) return st;
+      if (lv.Af.sg.ntiles > 0 && l < 63) c.info.staged_levels |= (int64_t)1 << l;
       if ((st = c.alloc(&lv.resf, lv.n))) return st;
       if ((st = c.alloc(&lv.outf, lv.n))) return st;
       if (c.o.smoother == 1 && (st = c.alloc(&lv.df, lv.n))) return st;
@@ -1582,6 +1710,8 @@ int amgf_options_default(amgf_options* o) {
   o->update_in_place = 1;
   o->smoother = 0;
   o->cheby_lower = 0.3;
+  o->stage_rows = 32;
+  o->stage_depth = 2;
   return AMGF_OK;
 }
 
@@ -1608,7 +1738,8 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
       opt.maxit < 0 || opt.contact_components < 0 || opt.contact_components > 2 || opt.precision < 0 ||
       opt.precision > 3 || opt.filter_algo < 0 || opt.filter_algo > 1 ||
       opt.interp < 0 || opt.interp > 1 || opt.p_max < 0 || opt.update_in_place < 0 || opt.update_in_place > 1 || opt.smoother < 0 ||
-      opt.smoother > 1 || !(opt.cheby_lower > 0.0 && opt.cheby_lower < 1.0))
+      opt.smoother > 1 || !(opt.cheby_lower > 0.0 && opt.cheby_lower < 1.0) || opt.stage_rows < 0 ||
+      opt.stage_rows > 4096 || (opt.stage_rows > 0 && (opt.stage_depth < 2 || opt.stage_depth > 8)))
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");
@@ -1810,8 +1941,11 @@ static int solve_device(Ctx& c, amgf_stats* stats) {
   CK(cudaMemcpyAsync(c.st_host, c.st, sizeof(PcgState), cudaMemcpyDeviceToHost, c.s));
   double res2[2] = {0.0, 0.0};
   CK(cudaMemcpyAsync(res2, c.scratch_scalar + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  int kerr = 0;
+  if (c.kerr) CK(cudaMemcpyAsync(&kerr, c.kerr, sizeof(int), cudaMemcpyDeviceToHost, c.s));
   CK(cudaStreamSynchronize(c.s));
   CK(cudaGetLastError());
+  if (kerr) return fail(AMGF_ERR_CUDA, "staged coarse-level sweep: a shared-memory pipeline wait timed out");
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, c.t0, c.t1));
   const PcgState& s = *c.st_host;
@@ -2028,6 +2162,11 @@ int amgf_time_kernel(amgf_handle h, int which, int warmup, int reps, void* strea
   float t = 0.f;
   CK(cudaEventElapsedTime(&t, c.t0, c.t1));
   *ms = t / reps;
+  if (c.kerr) {
+    int kerr = 0;
+    CK(cudaMemcpy(&kerr, c.kerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (kerr) return fail(AMGF_ERR_CUDA, "staged coarse-level sweep: a shared-memory pipeline wait timed out");
+  }
   // values (8 B) + column indices (4 B) per nonzero, row pointers, and each vector read/written once
   const double vec_bytes = which == 0 ? 2.0 * 8.0 * n : 4.0 * 8.0 * n;
   if (which == 3) {  // values (8, 4 or 2 B) + 4 B column per nonzero, row pointers, x, b, W, y

@@ -11,6 +11,9 @@
 //       POST      y = x + W (b - A x) [+ add]      (l1-Jacobi sweep; z = y2 + B r2)
 //     with W = diag(1 / l1), and optionally a deterministic dot product of the output
 //     with another vector (p^T A p, r^T z) finished by the last block to arrive.
+//   - csr_staged_kernel<MODE, VT, K, U>: the same sweeps (RESID, POST) for the BF16 coarse
+//     levels of the mixed V-cycle, with each tile of rows streamed into shared memory by a
+//     producer warp (cp.async.bulk + mbarrier) ahead of the consumer warps' gathers.
 //   - dense_gemv / dense_rows: coarsest-level solve with the host-computed inverse.
 //   - filter_bcr: one phase of the odd-even block cyclic reduction solve of the
 //     block-tridiagonal A_w (Section 5.1 filter step): all block GEMVs of a reduction
@@ -122,6 +125,8 @@ __device__ __forceinline__ void grid_dot_finish(double local, double* partial, d
 __device__ __forceinline__ double load_val(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float load_val(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float load_val(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename T, int K, int MODE, bool DOT, typename VT = T, int U = 4>
 __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T, VT> a) {
@@ -175,6 +180,251 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T, VT> a) {
     }
   }
   if (DOT) grid_dot_finish(dacc, a.partial, a.result, a.counter);
+}
+
+// ---------------- staged CSR sweeps of the FP32 V-cycle's coarse levels ----------------
+//
+// The coarse-level sweeps of the mixed-precision V-cycle (r = b - A x and the l1-Jacobi
+// post-smoother x + W (b - A x)) stream each row's column indices and values once and gather
+// x at those columns.  In csr_kernel every warp alternates between the two kinds of load, so
+// only part of the resident warps keep DRAM requests in flight.  Here one producer warp per
+// CTA streams whole tiles of consecutive rows (their row pointers, column indices, values and
+// the epilogue's b, x, W segments) into shared memory with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier), STAGE_DEPTH tiles ahead, while eight
+// consumer warps read the staged tile and issue only the gathers of x.  A lane sums the same
+// entries in the same order as csr_kernel with the same K, so both give identical results.
+//
+// Bulk copies start on 16-byte boundaries: each staged segment starts at the aligned index
+// at or below the first one the tile needs and is padded to whole 16-byte chunks; the device
+// arrays carry that padding (row pointers +2 entries, indices and values +16, vectors +8).
+
+constexpr int STAGE_NW = 8;                       // consumer warps per CTA
+constexpr int STAGE_TPB = (STAGE_NW + 1) * 32;    // + one producer warp
+constexpr int STAGE_MAX_DEPTH = 8;
+constexpr uint64_t STAGE_WAIT_NS = 4000000000ull; // a wait that has not completed in 4 s gives up
+
+struct StageArgs {
+  int64_t ntiles;
+  int rows;       // rows per tile
+  int depth;      // tiles in flight per CTA (<= STAGE_MAX_DEPTH)
+  int cap;        // staged index/value entries per tile (multiple of 8)
+  int rp_cap;     // staged row pointers per tile (even)
+  int vec_cap;    // staged entries of each epilogue vector per tile (multiple of 4)
+  int* err;       // set to 1 when a wait gave up (the host reports AMGF_ERR_CUDA)
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Wait for the phase of parity `parity` to complete; false when it has not after
+// STAGE_WAIT_NS (or 2^26 polls), so no wait can hang the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < (1u << 26); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u && global_ns() - t0 > STAGE_WAIT_NS) break;
+  }
+  return false;
+}
+// bulk asynchronous copy global -> this CTA's shared memory, completion counted on `bar`
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Byte layout of one stage: row pointers, column indices, values, then the epilogue vectors
+// (b for RESID; b, x, W for POST).  Every part is a multiple of 16 bytes.
+template <int MODE, typename VT>
+struct StageLayout {
+  static constexpr int nvec = MODE == M_POST ? 3 : 1;
+  __host__ __device__ static size_t bytes(int rp_cap, int cap, int vec_cap) {
+    return (size_t)rp_cap * 8 + (size_t)cap * (4 + sizeof(VT)) + (size_t)nvec * vec_cap * 4;
+  }
+};
+template <int MODE, typename VT>
+inline size_t stage_smem_bytes(const StageArgs& g) {
+  return 2 * STAGE_MAX_DEPTH * sizeof(uint64_t) + (size_t)g.depth * StageLayout<MODE, VT>::bytes(g.rp_cap, g.cap, g.vec_cap);
+}
+
+// MODE: M_RESID (y = b - A x) or M_POST (y = x + W (b - A x)); FP32 vectors, VT values.
+template <int MODE, typename VT, int K, int U>
+__global__ void __launch_bounds__(STAGE_TPB) csr_staged_kernel(CsrArgsT<float, VT> a, StageArgs g) {
+  static_assert(MODE == M_RESID || MODE == M_POST, "staged modes");
+  static_assert(K >= 2 && K <= 32 && (K & (K - 1)) == 0, "K must be a power of two <= 32");
+  extern __shared__ __align__(16) unsigned char stage_smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage_smem);
+  uint64_t* empty = full + STAGE_MAX_DEPTH;
+  unsigned char* stages = stage_smem + 2 * STAGE_MAX_DEPTH * sizeof(uint64_t);
+  const size_t sbytes = StageLayout<MODE, VT>::bytes(g.rp_cap, g.cap, g.vec_cap);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int depth = g.depth;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < depth; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, STAGE_NW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  auto stage_ptrs = [&](int s, int64_t*& rps, int32_t*& cis, VT*& vs, float*& bs, float*& xs, float*& ws) {
+    unsigned char* p = stages + (size_t)s * sbytes;
+    rps = reinterpret_cast<int64_t*>(p);
+    p += (size_t)g.rp_cap * 8;
+    cis = reinterpret_cast<int32_t*>(p);
+    p += (size_t)g.cap * 4;
+    vs = reinterpret_cast<VT*>(p);
+    p += (size_t)g.cap * sizeof(VT);
+    bs = reinterpret_cast<float*>(p);
+    xs = bs + g.vec_cap;
+    ws = xs + g.vec_cap;
+  };
+
+  if (warp == STAGE_NW) {
+    // producer: one lane issues the copies of this CTA's tiles, `depth` ahead of the consumers
+    if (lane != 0) return;
+    int64_t issued = 0;
+    // the next tile's nonzero range is loaded one tile ahead, so its latency overlaps the wait
+    // for a free stage
+    auto tile_rows = [&](int64_t t, int64_t& r0, int64_t& r1) {
+      r0 = t * g.rows;
+      r1 = r0 + g.rows < a.nrows ? r0 + g.rows : a.nrows;
+    };
+    int64_t k0n = 0, k1n = 0;
+    if ((int64_t)blockIdx.x < g.ntiles) {
+      int64_t r0, r1;
+      tile_rows(blockIdx.x, r0, r1);
+      k0n = __ldg(a.rp + r0);
+      k1n = __ldg(a.rp + r1);
+    }
+    for (int64_t j = 0;; ++j) {
+      const int64_t t = blockIdx.x + j * gridDim.x;
+      if (t >= g.ntiles) break;
+      const int64_t k0 = k0n, k1 = k1n;
+      if (t + gridDim.x < g.ntiles) {
+        int64_t r0n, r1n;
+        tile_rows(t + gridDim.x, r0n, r1n);
+        k0n = __ldg(a.rp + r0n);
+        k1n = __ldg(a.rp + r1n);
+      }
+      const int s = (int)(j % depth);
+      const int64_t q = j / depth;
+      if (q > 0 && !mbar_wait_bounded(empty + s, (uint32_t)((q - 1) & 1))) {
+        atomicExch(g.err, 1);
+        break;
+      }
+      int64_t r0, r1;
+      tile_rows(t, r0, r1);
+      const int64_t ka = k0 & ~(int64_t)7;
+      const int64_t kn = (k1 - ka + 7) & ~(int64_t)7;
+      const int64_t ra = r0 & ~(int64_t)1;
+      const int64_t rn = (r1 + 1 - ra + 1) & ~(int64_t)1;
+      const int64_t va = r0 & ~(int64_t)3;
+      const int64_t vn = (r1 - va + 3) & ~(int64_t)3;
+      const int nvec = StageLayout<MODE, VT>::nvec;
+      const uint32_t bytes = (uint32_t)(rn * 8 + kn * (4 + (int64_t)sizeof(VT)) + nvec * vn * 4);
+      int64_t* rps; int32_t* cis; VT* vs; float *bs, *xs, *ws;
+      stage_ptrs(s, rps, cis, vs, bs, xs, ws);
+      mbar_arrive_expect_tx(full + s, bytes);
+      bulk_to_smem(rps, a.rp + ra, (uint32_t)(rn * 8), full + s);
+      if (kn > 0) {
+        bulk_to_smem(cis, a.ci + ka, (uint32_t)(kn * 4), full + s);
+        bulk_to_smem(vs, a.v + ka, (uint32_t)(kn * sizeof(VT)), full + s);
+      }
+      bulk_to_smem(bs, a.b + va, (uint32_t)(vn * 4), full + s);
+      if (MODE == M_POST) {
+        bulk_to_smem(xs, a.x + va, (uint32_t)(vn * 4), full + s);
+        bulk_to_smem(ws, a.winv + va, (uint32_t)(vn * 4), full + s);
+      }
+      ++issued;
+    }
+    // no copy may still be landing in this CTA's shared memory when it exits: wait for the
+    // last phase issued into every stage
+    for (int s = 0; s < depth; ++s) {
+      const int64_t n_s = issued > s ? (issued - 1 - s) / depth + 1 : 0;  // issues into stage s
+      if (n_s > 0 && !mbar_wait_bounded(full + s, (uint32_t)((n_s - 1) & 1))) atomicExch(g.err, 1);
+    }
+    return;
+  }
+
+  // consumers: K lanes per row, rows of a tile spread over the eight warps
+  const int sub = lane & (K - 1);
+  constexpr int G = STAGE_NW * (32 / K);  // row groups per CTA
+  for (int64_t j = 0;; ++j) {
+    const int64_t t = blockIdx.x + j * gridDim.x;
+    if (t >= g.ntiles) break;
+    const int s = (int)(j % depth);
+    if (!mbar_wait_bounded(full + s, (uint32_t)((j / depth) & 1))) {
+      if (lane == 0) atomicExch(g.err, 1);
+      break;
+    }
+    int64_t* rps; int32_t* cis; VT* vs; float *bs, *xs, *ws;
+    stage_ptrs(s, rps, cis, vs, bs, xs, ws);
+    const int64_t r0 = t * g.rows;
+    const int nr = (int)(r0 + g.rows < a.nrows ? g.rows : a.nrows - r0);
+    const int roff = (int)(r0 & 1), voff = (int)(r0 & 3);
+    const int64_t ka = rps[roff] & ~(int64_t)7;
+    for (int base = warp * (32 / K); base < nr; base += G) {
+      const int rr = base + lane / K;
+      const bool valid = rr < nr;
+      float sum = 0.f;
+      if (valid) {
+        const int ke = (int)(rps[roff + rr + 1] - ka);
+        for (int kb = (int)(rps[roff + rr] - ka) + sub; kb < ke; kb += U * K) {
+          int32_t jj[U];
+          float vv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int k = kb + u * K;
+            const bool ok = k < ke;
+            jj[u] = ok ? cis[k] : -1;
+            vv[u] = ok ? to_float(vs[k]) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (jj[u] >= 0) sum += vv[u] * __ldg(a.x + jj[u]);
+        }
+      }
+#pragma unroll
+      for (int off = K / 2; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off, K);
+      if (valid && sub == 0) {
+        const int vi = voff + rr;
+        float out;
+        if (MODE == M_RESID) out = bs[vi] - sum;
+        else out = xs[vi] + ws[vi] * (bs[vi] - sum);
+        a.y[r0 + rr] = out;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + s);
+  }
 }
 
 // Fine-level operator in 3x3 node blocks (BSR3, slices of 32 block rows; see setup.h):

@@ -39,6 +39,8 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--weights", default=None, help="learned smoother weights (.npz), 'default' = packaged")
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--stage-rows", type=int, default=None, help="amgf_options.stage_rows (default: library's)")
+    ap.add_argument("--stage-depth", type=int, default=None, help="amgf_options.stage_depth")
     args = ap.parse_args(argv)
 
     import torch
@@ -51,7 +53,12 @@ def main(argv=None):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     fp64_peak = sms * 2 * 2 * mhz * 1e6  # flop/s
     p = cg.make_problem(args.config, seed=0)
-    s = amgf.Solver(p.K, p.J, p.D, precision=args.precision)
+    opts = {}
+    if args.stage_rows is not None:
+        opts["stage_rows"] = args.stage_rows
+    if args.stage_depth is not None:
+        opts["stage_depth"] = args.stage_depth
+    s = amgf.Solver(p.K, p.J, p.D, precision=args.precision, **opts)
     if args.weights:
         from paper_2505_18576_gb300.learned import load_weights
         default = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "smoother_c64.npz")
@@ -76,7 +83,7 @@ def main(argv=None):
           f"{', learned smoother' if args.weights else ''}: {st.iters} PCG iterations per solve, "
           f"{total_ms / args.iters:.3f} ms per profiled iteration ({args.iters} iterations), "
           f"copy-bandwidth peak {hbm:.1f} GB/s ({kind}), FP64 peak {fp64_peak / 1e12:.3f} TFLOP/s "
-          f"({sms} SMs, {mhz:.0f} MHz).\n")
+          f"({sms} SMs, {mhz:.0f} MHz); staged levels mask {int(s.info.staged_levels):#x}.\n")
     print("| operation | level | launches / iteration | us / launch | MB / launch | GB/s | of peak | FP64 pipe | share |")
     print("|---|---|---|---|---|---|---|---|---|")
     for (op, lvl), (cnt, ms, by, fl) in sorted(agg.items(), key=lambda kv: -kv[1][1]):

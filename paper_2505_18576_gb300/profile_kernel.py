@@ -28,6 +28,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--weights", default=None, help="learned smoother weights (.npz), 'default' = packaged")
+    ap.add_argument("--stage-rows", type=int, default=None, help="amgf_options.stage_rows (default: library's)")
+    ap.add_argument("--stage-depth", type=int, default=None, help="amgf_options.stage_depth")
     args = ap.parse_args(argv)
 
     import torch
@@ -37,7 +39,12 @@ def main(argv=None):
 
     torch.cuda.set_device(0)
     p = cg.make_problem(args.config, seed=0)
-    s = amgf.Solver(p.K, p.J, p.D, precision=args.precision)
+    opts = {}
+    if args.stage_rows is not None:
+        opts["stage_rows"] = args.stage_rows
+    if args.stage_depth is not None:
+        opts["stage_depth"] = args.stage_depth
+    s = amgf.Solver(p.K, p.J, p.D, precision=args.precision, **opts)
     if args.weights:
         from paper_2505_18576_gb300.learned import load_weights
         default = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "smoother_c64.npz")
@@ -46,7 +53,7 @@ def main(argv=None):
     info = s.info
     print(json.dumps({"config": args.config, "precision": args.precision, "which": args.which, "ms": ms,
                       "algorithmic_bytes_per_launch": nbytes, "gbs": nbytes / (ms * 1e-3) / 1e9,
-                      "levels": int(info.nlevels),
+                      "levels": int(info.nlevels), "staged_levels": int(info.staged_levels),
                       "level_rows": [int(info.level_rows[l]) for l in range(info.nlevels)],
                       "level_nnz": [int(info.level_nnz[l]) for l in range(info.nlevels)]}))
     s.close()

@@ -222,3 +222,15 @@ def test_host_filter_solve_matches_oracle(case, algo):
     assert np.linalg.norm(w - wo) <= max(1e-12, 16 * eps * ev[-1] / ev[0]) * np.linalg.norm(wo)
     s.close()
     o.close()
+
+
+def test_staged_sweep_options_rejected():
+    # stage_rows in [0, 4096], stage_depth in [2, 8] when staging is on; checked before any device use
+    p = cg.make_problem(None, seed=0, nx=4, ny=4, nz=2, d_lo=-2, d_hi=2)
+    for kw in (dict(stage_rows=-1), dict(stage_rows=5000), dict(stage_rows=32, stage_depth=1),
+               dict(stage_rows=32, stage_depth=9)):
+        with pytest.raises(amgf.AmgfError) as e:
+            amgf.Solver(p.K, p.J, p.D, precision=3, host_only=True, **kw)
+        assert e.value.status == 1
+    o = amgf.amgf_options_default()
+    assert (o.stage_rows, o.stage_depth) == (32, 2)

@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--weights", default=None, help="learned smoother weights (.npz), 'default' = packaged")
     ap.add_argument("--stage-rows", type=int, default=None, help="amgf_options.stage_rows (default: library's)")
     ap.add_argument("--stage-depth", type=int, default=None, help="amgf_options.stage_depth")
+    ap.add_argument("--set", action="append", default=[], metavar="FIELD=INT",
+                    help="any other integer field of amgf_options, e.g. --set fuse_tail=0")
     args = ap.parse_args(argv)
 
     import torch
@@ -44,6 +46,9 @@ def main(argv=None):
         opts["stage_rows"] = args.stage_rows
     if args.stage_depth is not None:
         opts["stage_depth"] = args.stage_depth
+    for kv in args.set:
+        k, v = kv.split("=", 1)
+        opts[k] = int(v)
     s = amgf.Solver(p.K, p.J, p.D, precision=args.precision, **opts)
     if args.weights:
         from paper_2505_18576_gb300.learned import load_weights

@@ -108,6 +108,12 @@ typedef struct {
                              of the CTA's row groups; 0: plain loads, csr_kernel, everywhere).
                              Same results either way.  At most 4096. */
   int stage_depth;        /* tiles in flight per CTA of the staged sweeps, 2..8 (2) */
+  int sell_window;        /* FP64 V-cycle: the long-row coarse levels with enough rows to give each
+                             GPU lane its own row are swept from a sliced-ELL copy (one lane per
+                             row, slices of 32 rows sorted by length within windows of this many
+                             rows; 256).  0: CSR with lane groups everywhere.  The per-row sums
+                             then run in CSR order in one FMA chain instead of in lane-interleaved
+                             partial sums, so the two forms differ by rounding. */
 } amgf_options;
 
 typedef struct {
@@ -142,6 +148,8 @@ typedef struct {
   double t_hierarchy_s;      /*           the AMG hierarchy */
   double t_filter_s;         /*           I_c, ordering and the A_w factor */
   int64_t staged_levels;     /* bit l set: the sweeps of level l run staged (amgf_options.stage_rows) */
+  int64_t sell_levels;       /* bit l set: level l's FP64 sweeps run from the sliced-ELL copy
+                                (amgf_options.sell_window) */
 } amgf_info;
 
 typedef struct amgf_ctx* amgf_handle;

@@ -57,7 +57,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("filter_algo", ctypes.c_int),
                 ("interp", ctypes.c_int), ("p_max", ctypes.c_int), ("update_in_place", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("cheby_lower", ctypes.c_double),
-                ("stage_rows", ctypes.c_int), ("stage_depth", ctypes.c_int)]
+                ("stage_rows", ctypes.c_int), ("stage_depth", ctypes.c_int), ("sell_window", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -79,7 +79,7 @@ class Info(ctypes.Structure):
                 ("filter_nblocks", ctypes.c_int64), ("op_complexity", ctypes.c_double),
                 ("t_setup_s", ctypes.c_double), ("t_assemble_s", ctypes.c_double),
                 ("t_hierarchy_s", ctypes.c_double), ("t_filter_s", ctypes.c_double),
-                ("staged_levels", ctypes.c_int64)]
+                ("staged_levels", ctypes.c_int64), ("sell_levels", ctypes.c_int64)]
 
 
 _lib = None

@@ -64,6 +64,14 @@ struct DCSR {
   int64_t* soff = nullptr;
   int32_t* bci = nullptr;
   double* bv = nullptr;
+  // optional sliced-ELL copy (sell_kernel) for the SPMV / RESID / POST sweeps of a long-row
+  // level; the CSR arrays stay for the other modes.  sell_h: host slice offsets and row
+  // permutation (values dropped) for in-place value updates.
+  int64_t* ell_soff = nullptr;
+  int32_t* ell_perm = nullptr;
+  int32_t* ell_ci = nullptr;
+  double* ell_v = nullptr;
+  SELL sell_h;
 };
 
 struct DCSRf {  // FP32 (or BF16) values: V-cycle levels of the mixed-precision solve
@@ -380,6 +388,22 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
                 A.nrows * (epilogue_bytes(MODE, a, 8.0) + (result ? 8.0 : 0.0)),
             2.0 * A.nnz);
     return;
+  }
+  if constexpr (MODE == M_SPMV || MODE == M_RESID || MODE == M_POST) {
+    if (A.ell_v && !a.rows && !result && !a.y2 && !a.yf && !a.y2f) {
+      SellArgs e{};
+      e.soff = A.ell_soff; e.perm = A.ell_perm; e.ci = A.ell_ci; e.v = A.ell_v;
+      e.nrows = A.nrows; e.nslices = A.sell_h.nslices;
+      e.x = a.x; e.b = a.b; e.winv = a.winv; e.add = a.add; e.y = a.y;
+      const int grid = grid_for(c, e.nslices, 32);  // one warp per slice
+      sell_kernel<MODE><<<grid, TPB, 0, c.s>>>(e);
+      // stored slots (values + columns, padding excluded), slice offsets, permutation, x once, epilogue
+      counted(c, op_label(A.role, MODE), A.level,
+              (double)A.nnz * 12.0 + (double)(e.nslices + 1) * 8.0 + 4.0 * A.nrows + 8.0 * A.ncols +
+                  A.nrows * epilogue_bytes(MODE, a, 8.0),
+              2.0 * A.nnz);
+      return;
+    }
   }
   const int grid = grid_for(c, A.nrows, A.K);
   if (result) {
@@ -1147,6 +1171,28 @@ static int plan_staging(Ctx& c, const HCSR& h, DCSRf& d) {
   return plan_staging_t<__nv_bfloat16>(c, d, g);
 }
 
+// Sliced ELL with rows sorted in windows of o.sell_window (sell_kernel) for the FP64 level
+// operators whose rows are long (>= SELL_MIN_AVG entries on average) and numerous enough to fill
+// the GPU with one lane per row (>= SELL_MIN_ROWS_PER_SM rows per SM); the other levels keep
+// csr_kernel.
+constexpr double SELL_MIN_AVG = 24.0;
+constexpr int64_t SELL_MIN_ROWS_PER_SM = 1024;
+static int plan_sell(Ctx& c, const HCSR& h, DCSR& d) {
+  if (c.o.sell_window <= 0 || h.nrows == 0 || h.nrows != h.ncols) return AMGF_OK;
+  if ((double)h.nnz() / (double)h.nrows < SELL_MIN_AVG || h.nrows < SELL_MIN_ROWS_PER_SM * c.num_sms) return AMGF_OK;
+  if (h.nrows > (int64_t)INT32_MAX) return AMGF_OK;
+  build_sell(h, c.o.sell_window, d.sell_h);
+  int st;
+  if ((st = c.upload(&d.ell_soff, d.sell_h.soff.data(), d.sell_h.nslices + 1))) return st;
+  if ((st = c.upload(&d.ell_perm, d.sell_h.perm.data(), h.nrows))) return st;
+  if ((st = c.upload(&d.ell_ci, d.sell_h.ci.data(), (int64_t)d.sell_h.ci.size()))) return st;
+  if ((st = c.upload(&d.ell_v, d.sell_h.v.data(), (int64_t)d.sell_h.v.size()))) return st;
+  std::vector<int32_t>().swap(d.sell_h.ci);  // the device copy is the only one used
+  std::vector<double>().swap(d.sell_h.v);
+  std::vector<int32_t>().swap(d.sell_h.perm);
+  return AMGF_OK;
+}
+
 static void fill_info(Ctx& c) {
   amgf_info& in = c.info;
   std::memset(&in, 0, sizeof in);
@@ -1162,8 +1208,10 @@ static void fill_info(Ctx& c) {
   in.op_complexity = tot / (double)c.H.A[0].nnz();
   in.filter_block = c.F.nb;
   in.filter_nblocks = c.F.nblk;
-  for (size_t l = 0; l < c.L.size() && l < 63; ++l)
+  for (size_t l = 0; l < c.L.size() && l < 63; ++l) {
     if (c.L[l].Af.sg.ntiles > 0) in.staged_levels |= (int64_t)1 << l;
+    if (c.L[l].A.ell_v) in.sell_levels |= (int64_t)1 << l;
+  }
 }
 
 // dst[idx[k]] = val[k] on the device (temporary buffers, synchronous)
@@ -1283,6 +1331,14 @@ static int update_D_in_place(Ctx& c, const double* D, const amgf_csr& K, const a
       std::vector<double> val(idx.size());
       for (size_t k = 0; k < idx.size(); ++k) val[k] = A.v[idx[k]];
       if ((st = scatter_to_device(c, lv.A.v, idx, val))) return st;
+      if (lv.A.ell_v) {  // the same values at their sliced-ELL slots
+        std::vector<int64_t> slots(idx.size());
+        for (size_t k = 0; k < idx.size(); ++k) {
+          const int64_t r = (int64_t)(std::upper_bound(A.rp.begin(), A.rp.end(), idx[k]) - A.rp.begin()) - 1;
+          slots[k] = sell_slot(A, lv.A.sell_h, r, idx[k]);
+        }
+        if ((st = scatter_to_device(c, lv.A.ell_v, slots, val))) return st;
+      }
     } else if (lv.Af.vb) {
       std::vector<__nv_bfloat16> val(idx.size());
       for (size_t k = 0; k < idx.size(); ++k) val[k] = __float2bfloat16_rn((float)A.v[idx[k]]);
@@ -1416,6 +1472,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   // ---- device upload
   c.release_device();
   c.info.staged_levels = 0;
+  c.info.sell_levels = 0;
   c.bsr0 = BSR3();
   const int nlev = c.H.nlev();
   c.L.assign(nlev, DLevel());
@@ -1445,7 +1502,10 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
         c.bsr0 = std::move(bsr);  // for in-place updates of the contact rows
       } else if ((st = upload_csr(c, c.H.A[l], lv.A))) {
         return st;
+      } else if (l > 0 && (st = plan_sell(c, c.H.A[l], lv.A))) {
+        return st;
       }
+      if (lv.A.ell_v && l < 63) c.info.sell_levels |= (int64_t)1 << l;
       if ((st = c.upload(&lv.winv, w.data(), lv.n))) return st;
       if ((st = c.alloc(&lv.x, lv.n))) return st;
     }
@@ -1712,6 +1772,7 @@ int amgf_options_default(amgf_options* o) {
   o->cheby_lower = 0.3;
   o->stage_rows = 32;
   o->stage_depth = 2;
+  o->sell_window = 256;
   return AMGF_OK;
 }
 
@@ -1739,7 +1800,8 @@ static int setup_impl(const amgf_csr* K, const amgf_csr* J, const double* D, con
       opt.precision > 3 || opt.filter_algo < 0 || opt.filter_algo > 1 ||
       opt.interp < 0 || opt.interp > 1 || opt.p_max < 0 || opt.update_in_place < 0 || opt.update_in_place > 1 || opt.smoother < 0 ||
       opt.smoother > 1 || !(opt.cheby_lower > 0.0 && opt.cheby_lower < 1.0) || opt.stage_rows < 0 ||
-      opt.stage_rows > 4096 || (opt.stage_rows > 0 && (opt.stage_depth < 2 || opt.stage_depth > 8)))
+      opt.stage_rows > 4096 || (opt.stage_rows > 0 && (opt.stage_depth < 2 || opt.stage_depth > 8)) ||
+      opt.sell_window < 0)
     return fail(AMGF_ERR_INVALID_ARG, "invalid options");
   int ndev = 0;
   if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) return fail(AMGF_ERR_CUDA, "no CUDA device");

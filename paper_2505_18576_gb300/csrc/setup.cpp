@@ -664,6 +664,54 @@ int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<dou
 
 }  // namespace
 
+void build_sell(const HCSR& A, int64_t window, SELL& out) {
+  out = SELL();
+  const int64_t n = A.nrows;
+  out.nrows = n;
+  out.nslices = (n + SELL::C - 1) / SELL::C;
+  out.perm.resize(n);
+  out.pinv.resize(n);
+  for (int64_t i = 0; i < n; ++i) out.perm[i] = (int32_t)i;
+  if (window < 1) window = 1;
+  for (int64_t a = 0; a < n; a += window) {
+    const int64_t b = std::min(n, a + window);
+    std::stable_sort(out.perm.begin() + a, out.perm.begin() + b, [&](int32_t x, int32_t y) {
+      return A.rp[x + 1] - A.rp[x] > A.rp[y + 1] - A.rp[y];
+    });
+  }
+  for (int64_t q = 0; q < n; ++q) out.pinv[out.perm[q]] = (int32_t)q;
+  out.soff.assign(out.nslices + 1, 0);
+  for (int64_t s = 0; s < out.nslices; ++s) {
+    int64_t w = 0;
+    for (int64_t q = s * SELL::C; q < std::min(n, (s + 1) * SELL::C); ++q) {
+      const int64_t r = out.perm[q];
+      w = std::max(w, A.rp[r + 1] - A.rp[r]);
+    }
+    out.soff[s + 1] = out.soff[s] + SELL::C * w;
+  }
+  const int64_t slots = out.soff[out.nslices];
+  out.ci.assign(slots, 0);
+  out.v.assign(slots, 0.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t s = 0; s < out.nslices; ++s) {
+    const int64_t w = (out.soff[s + 1] - out.soff[s]) / SELL::C;
+    for (int64_t lane = 0; lane < SELL::C; ++lane) {
+      const int64_t q = s * SELL::C + lane;
+      if (q >= n) continue;
+      const int64_t r = out.perm[q], len = A.rp[r + 1] - A.rp[r];
+      for (int64_t j = 0; j < w; ++j) {
+        const int64_t slot = out.soff[s] + SELL::C * j + lane;
+        if (j < len) {
+          out.ci[slot] = A.ci[A.rp[r] + j];
+          out.v[slot] = A.v[A.rp[r] + j];
+        } else {
+          out.ci[slot] = (int32_t)r;
+        }
+      }
+    }
+  }
+}
+
 bool build_bsr3(const HCSR& A, double max_fill, BSR3& out) {
   out = BSR3();
   if (A.nrows % 3 != 0 || A.nrows != A.ncols || A.nrows == 0) return false;

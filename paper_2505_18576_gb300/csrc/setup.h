@@ -86,6 +86,29 @@ bool build_bsr3(const HCSR& A, double max_fill, BSR3& out);
 // matrix with A's pattern): 9 * 32 * w_sl doubles in the order of BSR3::v from out on.
 void bsr3_fill_slice(const HCSR& A, const BSR3& L, int64_t sl, double* out);
 
+// Sliced ELL with one GPU lane per row (SELL-32-sigma): rows are sorted by length, longest first,
+// within windows of `window` consecutive rows (ties keep their order), and cut into slices of
+// 32 sorted rows.  Slice s has width w_s (its longest row) and owns 32 w_s slots from soff[s]:
+// entry j of sorted row 32 s + lane sits in slot soff[s] + 32 j + lane, entries in the row's
+// CSR order.  Slots past a row's end hold 0.0 and the row's own column (a square matrix); the
+// slots of the rows missing from the last slice hold 0.0 and column 0.  perm maps a sorted row
+// to its row of A, pinv the other way.
+struct SELL {
+  static constexpr int64_t C = 32;
+  int64_t nrows = 0, nslices = 0;
+  std::vector<int64_t> soff;     // nslices + 1, multiples of C
+  std::vector<int32_t> perm, pinv;
+  std::vector<int32_t> ci;
+  std::vector<double> v;
+};
+void build_sell(const HCSR& A, int64_t window, SELL& out);
+
+// Slot of A's CSR entry k (row r: rp[r] <= k < rp[r + 1]) in a SELL built from A.
+inline int64_t sell_slot(const HCSR& A, const SELL& S, int64_t r, int64_t k) {
+  const int64_t q = S.pinv[r];
+  return S.soff[q / SELL::C] + SELL::C * (k - A.rp[r]) + q % SELL::C;
+}
+
 // Input validation; returns an amgf_status.
 int validate_csr(const amgf_csr* a, const char* name, bool square, std::string& err);
 

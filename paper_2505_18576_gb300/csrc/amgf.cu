@@ -84,6 +84,13 @@ struct DCSRf {  // FP32 (or BF16) values: V-cycle levels of the mixed-precision 
   __nv_bfloat16* vb = nullptr;  // BF16 values instead of v (precision 3)
   int K = 4;
   int U = 4;                    // entries per lane and batch (8: long rows on a warp per row)
+  // optional sliced-ELL copy (sell_kernel) of an interpolation or restriction operator
+  int64_t* ell_soff = nullptr;
+  int32_t* ell_perm = nullptr;
+  int32_t* ell_ci = nullptr;
+  float* ell_v = nullptr;
+  __nv_bfloat16* ell_vb = nullptr;
+  int64_t ell_nslices = 0;
   // staged sweeps (csr_staged_kernel) of a level operator; sg.ntiles == 0: csr_kernel
   StageArgs sg{};
   int sgrid = 0;
@@ -389,14 +396,14 @@ static void launch_csr(Ctx& c, const DCSR& A, CsrArgs a, const double* dotv = nu
             2.0 * A.nnz);
     return;
   }
-  if constexpr (MODE == M_SPMV || MODE == M_RESID || MODE == M_POST) {
-    if (A.ell_v && !a.rows && !result && !a.y2 && !a.yf && !a.y2f) {
+  if constexpr (MODE == M_SPMV || MODE == M_SPMV_ADD || MODE == M_SPMV_W || MODE == M_RESID || MODE == M_POST) {
+    if (A.ell_v && !a.rows && !result && (MODE == M_SPMV_W || !a.y2) && !a.yf && !a.y2f) {
       SellArgs e{};
       e.soff = A.ell_soff; e.perm = A.ell_perm; e.ci = A.ell_ci; e.v = A.ell_v;
       e.nrows = A.nrows; e.nslices = A.sell_h.nslices;
-      e.x = a.x; e.b = a.b; e.winv = a.winv; e.add = a.add; e.y = a.y;
+      e.x = a.x; e.b = a.b; e.winv = a.winv; e.w2 = a.w2; e.add = a.add; e.y = a.y; e.y2 = a.y2;
       const int grid = grid_for(c, e.nslices, 32);  // one warp per slice
-      sell_kernel<MODE><<<grid, TPB, 0, c.s>>>(e);
+      sell_kernel<double, double, MODE><<<grid, TPB, 0, c.s>>>(e);
       // stored slots (values + columns, padding excluded), slice offsets, permutation, x once, epilogue
       counted(c, op_label(A.role, MODE), A.level,
               (double)A.nnz * 12.0 + (double)(e.nslices + 1) * 8.0 + 4.0 * A.nrows + 8.0 * A.ncols +
@@ -447,6 +454,25 @@ static void launch_csr_f(Ctx& c, const DCSRf& A, CsrArgsT<float> a) {
   const double vb = A.vb ? 2.0 : 4.0;
   const double bytes = (double)A.nnz * (vb + 4.0) + (double)(A.nrows + 1) * 8.0 + 4.0 * A.ncols +
                        A.nrows * epilogue_bytes(MODE, a, 4.0);
+  if constexpr (MODE == M_SPMV || MODE == M_SPMV_ADD || MODE == M_SPMV_W) {
+    if ((A.ell_v || A.ell_vb) && !a.rows && (MODE == M_SPMV_W || !a.y2) && !a.yf && !a.y2f) {
+      const int g = grid_for(c, A.ell_nslices, 32);  // one warp per slice
+      auto go = [&](auto* vals) {
+        using V = std::remove_const_t<std::remove_pointer_t<decltype(vals)>>;
+        SellArgsT<float, V> e{};
+        e.soff = A.ell_soff; e.perm = A.ell_perm; e.ci = A.ell_ci; e.v = vals;
+        e.nrows = A.nrows; e.nslices = A.ell_nslices;
+        e.x = a.x; e.b = a.b; e.winv = a.winv; e.w2 = a.w2; e.add = a.add; e.y = a.y; e.y2 = a.y2;
+        sell_kernel<float, V, MODE><<<g, TPB, 0, c.s>>>(e);
+      };
+      if (A.ell_vb) go(A.ell_vb); else go(A.ell_v);
+      counted(c, op_label(A.role, MODE), A.level,
+              (double)A.nnz * (vb + 4.0) + (double)(A.ell_nslices + 1) * 8.0 + 4.0 * A.nrows + 4.0 * A.ncols +
+                  A.nrows * epilogue_bytes(MODE, a, 4.0),
+              2.0 * A.nnz);
+      return;
+    }
+  }
   // level operator sweeps with plain epilogues: staged tiles (csr_staged_kernel)
   constexpr bool kStagedMode = MODE == M_RESID || MODE == M_POST;
   const bool staged = kStagedMode && A.sg.ntiles > 0 && !a.rows && !a.add && !a.y2 && !a.yf && !a.y2f;
@@ -1171,15 +1197,16 @@ static int plan_staging(Ctx& c, const HCSR& h, DCSRf& d) {
   return plan_staging_t<__nv_bfloat16>(c, d, g);
 }
 
-// Sliced ELL with rows sorted in windows of o.sell_window (sell_kernel) for the FP64 level
-// operators whose rows are long (>= SELL_MIN_AVG entries on average) and numerous enough to fill
-// the GPU with one lane per row (>= SELL_MIN_ROWS_PER_SM rows per SM); the other levels keep
-// csr_kernel.
+// Sliced ELL with rows sorted in windows of o.sell_window (sell_kernel) for the FP64 operators
+// with enough rows to fill the GPU with one lane per row (>= SELL_MIN_ROWS_PER_SM rows per SM):
+// the long-row level operators (>= SELL_MIN_AVG entries per row on average; `level_op`) and the
+// interpolation and restriction operators; the others keep csr_kernel.
 constexpr double SELL_MIN_AVG = 24.0;
 constexpr int64_t SELL_MIN_ROWS_PER_SM = 1024;
-static int plan_sell(Ctx& c, const HCSR& h, DCSR& d) {
-  if (c.o.sell_window <= 0 || h.nrows == 0 || h.nrows != h.ncols) return AMGF_OK;
-  if ((double)h.nnz() / (double)h.nrows < SELL_MIN_AVG || h.nrows < SELL_MIN_ROWS_PER_SM * c.num_sms) return AMGF_OK;
+static int plan_sell(Ctx& c, const HCSR& h, DCSR& d, bool level_op = true) {
+  if (c.o.sell_window <= 0 || h.nrows == 0) return AMGF_OK;
+  if (level_op && (h.nrows != h.ncols || (double)h.nnz() / (double)h.nrows < SELL_MIN_AVG)) return AMGF_OK;
+  if (h.nrows < SELL_MIN_ROWS_PER_SM * c.num_sms) return AMGF_OK;
   if (h.nrows > (int64_t)INT32_MAX) return AMGF_OK;
   build_sell(h, c.o.sell_window, d.sell_h);
   int st;
@@ -1190,6 +1217,29 @@ static int plan_sell(Ctx& c, const HCSR& h, DCSR& d) {
   std::vector<int32_t>().swap(d.sell_h.ci);  // the device copy is the only one used
   std::vector<double>().swap(d.sell_h.v);
   std::vector<int32_t>().swap(d.sell_h.perm);
+  return AMGF_OK;
+}
+
+// The same sliced-ELL copy for an interpolation or restriction operator of the FP32 V-cycle
+// (FP32 or BF16 values, as the CSR copy).
+static int plan_sell_f(Ctx& c, const HCSR& h, DCSRf& d) {
+  if (c.o.sell_window <= 0 || h.nrows == 0 || h.nrows < SELL_MIN_ROWS_PER_SM * c.num_sms) return AMGF_OK;
+  if (h.nrows > (int64_t)INT32_MAX) return AMGF_OK;
+  SELL S;
+  build_sell(h, c.o.sell_window, S);
+  int st;
+  if ((st = c.upload(&d.ell_soff, S.soff.data(), S.nslices + 1))) return st;
+  if ((st = c.upload(&d.ell_perm, S.perm.data(), h.nrows))) return st;
+  if ((st = c.upload(&d.ell_ci, S.ci.data(), (int64_t)S.ci.size()))) return st;
+  if (c.o.precision == 3) {
+    std::vector<__nv_bfloat16> v(S.v.size());
+    for (size_t k = 0; k < v.size(); ++k) v[k] = __float2bfloat16_rn((float)S.v[k]);
+    if ((st = c.upload(&d.ell_vb, v.data(), (int64_t)v.size()))) return st;
+  } else {
+    std::vector<float> v(S.v.begin(), S.v.end());
+    if ((st = c.upload(&d.ell_v, v.data(), (int64_t)v.size()))) return st;
+  }
+  d.ell_nslices = S.nslices;
   return AMGF_OK;
 }
 
@@ -1513,6 +1563,8 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       if (l + 1 < nlev) {
         if ((st = upload_csr(c, c.H.P[l], lv.P))) return st;
         if ((st = upload_csr(c, c.H.R[l], lv.R))) return st;
+        if ((st = plan_sell(c, c.H.P[l], lv.P, false))) return st;
+        if ((st = plan_sell(c, c.H.R[l], lv.R, false))) return st;
       }
       if ((st = c.alloc(&lv.rhs, lv.n))) return st;
       if ((st = c.alloc(&lv.res, lv.n))) return st;
@@ -1523,6 +1575,8 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       if (l + 1 < nlev) {
         if ((st = upload_csr_f(c, c.H.P[l], lv.Pf))) return st;
         if ((st = upload_csr_f(c, c.H.R[l], lv.Rf))) return st;
+        if ((st = plan_sell_f(c, c.H.P[l], lv.Pf))) return st;
+        if ((st = plan_sell_f(c, c.H.R[l], lv.Rf))) return st;
       }
       std::vector<float> wf(w.begin(), w.end());
       // W, b and x of a level are staged in 16-byte segments by the staged sweeps

@@ -189,37 +189,48 @@ __global__ void __launch_bounds__(TPB) csr_kernel(CsrArgsT<T, VT> a) {
 // length sharing a warp, partial batches and the shuffle reduction.  Here each lane owns one
 // row of a slice of 32 rows sorted by length (SELL, see setup.h), walks it with one FMA per
 // entry in CSR order (4 entries' loads in flight at a time), and runs the epilogue itself;
-// every warp load of values or columns is one contiguous 256- or 128-byte segment.
-struct SellArgs {
+// every warp load of values or columns is one contiguous 256- or 128-byte segment.  The same
+// form serves the short-row interpolation and restriction operators of the large levels, where
+// it replaces csr_kernel's chain of dependent loads (row pointers, then entries, then x).
+template <typename T, typename VT>
+struct SellArgsT {
   const int64_t* __restrict__ soff;
   const int32_t* __restrict__ perm;  // sorted row -> row of A
   const int32_t* __restrict__ ci;
-  const double* __restrict__ v;
+  const VT* __restrict__ v;          // stored values (FP64, FP32 or BF16)
   int64_t nrows, nslices;
-  const double* x;
-  const double* b;
-  const double* winv;
-  const double* add;
-  double* y;
+  const T* x;
+  const T* b;
+  const T* winv;
+  const T* w2;
+  const T* add;
+  T* y;
+  T* y2;
 };
+using SellArgs = SellArgsT<double, double>;
 
-// MODE: M_SPMV (y = A x), M_RESID (y = b - A x) or M_POST (y = x + W (b - A x) [+ add])
-template <int MODE>
-__global__ void __launch_bounds__(TPB) sell_kernel(SellArgs a) {
-  static_assert(MODE == M_SPMV || MODE == M_RESID || MODE == M_POST, "sell modes");
+__device__ __forceinline__ double sell_val(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float sell_val(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float sell_val(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+// MODE: M_SPMV (y = A x), M_SPMV_ADD (y += A x, prolongation), M_SPMV_W (y = A x, y2 = w2 y,
+// restriction), M_RESID (y = b - A x) or M_POST (y = x + W (b - A x) [+ add]).  T: vectors and
+// arithmetic (FP64, or FP32 in the mixed V-cycle); VT: stored values.
+template <typename T, typename VT, int MODE>
+__global__ void __launch_bounds__(TPB) sell_kernel(SellArgsT<T, VT> a) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * TPB) >> 5;
   for (int64_t s = w0; s < a.nslices; s += nw) {
     const int64_t s0 = __ldg(a.soff + s), w = (__ldg(a.soff + s + 1) - s0) >> 5;
     const int32_t* cp = a.ci + s0 + lane;
-    const double* vp = a.v + s0 + lane;
-    double acc = 0.0;
+    const VT* vp = a.v + s0 + lane;
+    T acc = T(0);
     int64_t j = 0;
     for (; j + 4 <= w; j += 4) {
       const int32_t c0 = __ldg(cp), c1 = __ldg(cp + 32), c2 = __ldg(cp + 64), c3 = __ldg(cp + 96);
-      const double v0 = __ldg(vp), v1 = __ldg(vp + 32), v2 = __ldg(vp + 64), v3 = __ldg(vp + 96);
-      const double x0 = __ldg(a.x + c0), x1 = __ldg(a.x + c1), x2 = __ldg(a.x + c2), x3 = __ldg(a.x + c3);
+      const T v0 = sell_val(vp), v1 = sell_val(vp + 32), v2 = sell_val(vp + 64), v3 = sell_val(vp + 96);
+      const T x0 = __ldg(a.x + c0), x1 = __ldg(a.x + c1), x2 = __ldg(a.x + c2), x3 = __ldg(a.x + c3);
       acc = fma(v0, x0, acc);
       acc = fma(v1, x1, acc);
       acc = fma(v2, x2, acc);
@@ -228,18 +239,20 @@ __global__ void __launch_bounds__(TPB) sell_kernel(SellArgs a) {
       vp += 128;
     }
     for (; j < w; ++j) {
-      acc = fma(__ldg(vp), __ldg(a.x + __ldg(cp)), acc);
+      acc = fma((T)sell_val(vp), __ldg(a.x + __ldg(cp)), acc);
       cp += 32;
       vp += 32;
     }
     const int64_t q = s * 32 + lane;
     if (q < a.nrows) {
       const int64_t o = __ldg(a.perm + q);
-      double out;
-      if (MODE == M_SPMV) out = acc;
+      T out;
+      if (MODE == M_SPMV || MODE == M_SPMV_W) out = acc;
+      else if (MODE == M_SPMV_ADD) out = a.y[o] + acc;
       else if (MODE == M_RESID) out = a.b[o] - acc;
       else { out = a.x[o] + a.winv[o] * (a.b[o] - acc); if (a.add) out += a.add[o]; }
       a.y[o] = out;
+      if (MODE == M_SPMV_W && a.y2) a.y2[o] = a.w2[o] * out;
     }
   }
 }

@@ -705,7 +705,7 @@ void build_sell(const HCSR& A, int64_t window, SELL& out) {
           out.ci[slot] = A.ci[A.rp[r] + j];
           out.v[slot] = A.v[A.rp[r] + j];
         } else {
-          out.ci[slot] = (int32_t)r;
+          out.ci[slot] = len > 0 ? A.ci[A.rp[r]] : 0;
         }
       }
     }

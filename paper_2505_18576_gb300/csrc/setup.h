@@ -90,9 +90,10 @@ void bsr3_fill_slice(const HCSR& A, const BSR3& L, int64_t sl, double* out);
 // within windows of `window` consecutive rows (ties keep their order), and cut into slices of
 // 32 sorted rows.  Slice s has width w_s (its longest row) and owns 32 w_s slots from soff[s]:
 // entry j of sorted row 32 s + lane sits in slot soff[s] + 32 j + lane, entries in the row's
-// CSR order.  Slots past a row's end hold 0.0 and the row's own column (a square matrix); the
-// slots of the rows missing from the last slice hold 0.0 and column 0.  perm maps a sorted row
-// to its row of A, pinv the other way.
+// CSR order.  Slots past a row's end hold 0.0 and the row's first column (so a padded row reads
+// only entries of x it uses anyway; column 0 for an empty row); the slots of the rows missing
+// from the last slice hold 0.0 and column 0.  perm maps a sorted row to its row of A, pinv the
+// other way.
 struct SELL {
   static constexpr int64_t C = 32;
   int64_t nrows = 0, nslices = 0;

@@ -278,6 +278,15 @@ def load_traffic(kind: str, precision: int, bytes_now: float):
         return None, None
 
 
+def level1_kernel(s) -> str:
+    """Name of the kernel that runs the level-1 sweeps of this handle."""
+    if int(s.info.sell_levels) & 2:
+        return "sell_kernel<POST> (sliced ELL, one lane per row)"
+    if int(s.info.staged_levels) & 2:
+        return "csr_staged_kernel<POST> (tiles staged by cp.async.bulk)"
+    return "csr_kernel<POST>"
+
+
 def roofline_of(s, which: int, kind: str, precision: int, hbm_peak: float, peak_kind: str, sm_count: int,
                 sm_mhz: float, label: str):
     kms, kbytes = s.time_kernel(which, warmup=5, reps=50)
@@ -392,7 +401,7 @@ def run_gpu(args, rank, world, local):
     roofline_coarse = None
     if info.nlevels >= 3:
         roofline_coarse = roofline_of(s, 3, "level1", args.precision, hbm_peak, peak_kind, sm_count, sm_mhz,
-                                      f"csr_kernel<POST>: level-1 l1-Jacobi sweep ({PRECISIONS[args.precision]})")
+                                      f"{level1_kernel(s)}: level-1 l1-Jacobi sweep ({PRECISIONS[args.precision]})")
 
     # the same workload with the other V-cycle precisions / the learned smoother (same timing method,
     # fewer steps), each with its A-norm distance to the timed configuration's solution of seed 0.
@@ -463,7 +472,7 @@ def run_gpu(args, rank, world, local):
                                           f"({PRECISIONS[prec]}, FP64 contact term)")
             if sv.info.nlevels >= 3:
                 ent["roofline_coarse"] = roofline_of(sv, 3, "level1", prec, hbm_peak, peak_kind, sm_count, sm_mhz,
-                                                     f"csr_kernel<POST>: level-1 l1-Jacobi sweep ({PRECISIONS[prec]})")
+                                                     f"{level1_kernel(sv)}: level-1 l1-Jacobi sweep ({PRECISIONS[prec]})")
         variants[name] = ent
         sv.close()
         del sv, xv

@@ -88,7 +88,8 @@ def main(argv=None):
           f"{', learned smoother' if args.weights else ''}: {st.iters} PCG iterations per solve, "
           f"{total_ms / args.iters:.3f} ms per profiled iteration ({args.iters} iterations), "
           f"copy-bandwidth peak {hbm:.1f} GB/s ({kind}), FP64 peak {fp64_peak / 1e12:.3f} TFLOP/s "
-          f"({sms} SMs, {mhz:.0f} MHz); staged levels mask {int(s.info.staged_levels):#x}.\n")
+          f"({sms} SMs, {mhz:.0f} MHz); staged levels mask {int(s.info.staged_levels):#x}, "
+          f"sliced-ELL levels mask {int(s.info.sell_levels):#x}.\n")
     print("| operation | level | launches / iteration | us / launch | MB / launch | GB/s | of peak | FP64 pipe | share |")
     print("|---|---|---|---|---|---|---|---|---|")
     for (op, lvl), (cnt, ms, by, fl) in sorted(agg.items(), key=lambda kv: -kv[1][1]):

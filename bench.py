@@ -19,6 +19,8 @@ between steps.  Prints one JSON line (rank 0).  Besides the contract's keys it c
     apart, the scale below which solutions cannot be told apart in FP64;
   - `roofline` (the FP64 fine-level sweep against the measured HBM copy bandwidth, with its
     FP64-pipe fraction as a secondary figure) and `roofline_coarse` (the level-1 sweep);
+  - `iteration`: the algorithmic bytes (and flops, launches) of one PCG iteration summed over its
+    launches, next to the timed seconds per iteration and the bandwidth that implies;
   - `cpu_baseline`: the CPU FP64 oracle on the host cores -- one complete PCG solve of the
     same system on all cores (setup reported separately) and a single-threaded sample.
 
@@ -314,6 +316,21 @@ def roofline_of(s, which: int, kind: str, precision: int, hbm_peak: float, peak_
     return out
 
 
+def iteration_model(s, s_per_iter: float, hbm_peak: float):
+    """The bytes model of one PCG iteration next to its measured time: algorithmic bytes and flops
+    summed over every launch of one iteration (amgf_profile_iteration records them launch by
+    launch), over the timed solve's seconds per iteration."""
+    recs = s.profile_iteration()
+    by = sum(r["bytes"] for r in recs)
+    fl = sum(r["flops"] for r in recs)
+    gbs = by / s_per_iter / 1e9
+    return {"algorithmic_bytes": round(by), "flops": round(fl), "launches": len(recs),
+            "s_per_iteration": s_per_iter, "achieved_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm_peak, 4),
+            "note": "bytes: stored values and indices at their precision, one read of every input vector, "
+                    "one write of every output, summed over the launches of one iteration; time: the timed "
+                    "solves' seconds per PCG iteration (includes the initial residual and apply)"}
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -402,6 +419,7 @@ def run_gpu(args, rank, world, local):
     if info.nlevels >= 3:
         roofline_coarse = roofline_of(s, 3, "level1", args.precision, hbm_peak, peak_kind, sm_count, sm_mhz,
                                       f"{level1_kernel(s)}: level-1 l1-Jacobi sweep ({PRECISIONS[args.precision]})")
+    iteration = iteration_model(s, ms * 1e-3 / max(1e-9, statistics.mean(iters)), hbm_peak)
 
     # the same workload with the other V-cycle precisions / the learned smoother (same timing method,
     # fewer steps), each with its A-norm distance to the timed configuration's solution of seed 0.
@@ -473,6 +491,7 @@ def run_gpu(args, rank, world, local):
             if sv.info.nlevels >= 3:
                 ent["roofline_coarse"] = roofline_of(sv, 3, "level1", prec, hbm_peak, peak_kind, sm_count, sm_mhz,
                                                      f"{level1_kernel(sv)}: level-1 l1-Jacobi sweep ({PRECISIONS[prec]})")
+        ent["iteration"] = iteration_model(sv, ent["s_per_solve"] / max(1e-9, statistics.mean(its)), hbm_peak)
         variants[name] = ent
         sv.close()
         del sv, xv
@@ -501,6 +520,7 @@ def run_gpu(args, rank, world, local):
         }
         if roofline_coarse:
             line["roofline_coarse"] = roofline_coarse
+        line["iteration"] = iteration
         if variants:
             line["variants"] = variants
             line["a_norm_rounding_floor"] = floor

@@ -32,12 +32,21 @@ pytestmark = pytest.mark.gpu
 EPS = np.finfo(np.float64).eps
 
 
-def test_c96_vcycle_and_apply_stages():
-    import paper_2505_18576_gb300 as m
-    from test_gpu_stages import check_stages
+@pytest.fixture(scope="module")
+def c96():
     p = cg.make_problem("c96", seed=0)
     o = oracle.Oracle(p.K, p.J, p.D)
+    yield p, o
+    o.close()
+
+
+def test_c96_vcycle_and_apply_stages(c96):
+    import paper_2505_18576_gb300 as m
+    from test_gpu_stages import check_stages
+    p, o = c96
     s = m.Solver(p.K, p.J, p.D)
+    # at this size levels 1-2 and the interpolation of levels 0-1 run in the sliced-ELL layout
+    assert int(s.info.sell_levels) & 2
     try:
         assert s.info.nlevels == o.nlev
         r = np.random.default_rng(6).standard_normal(p.n)
@@ -51,7 +60,31 @@ def test_c96_vcycle_and_apply_stages():
         assert err <= 1e-12
     finally:
         s.close()
-        o.close()
+
+
+def test_c96_bf16_vcycle_and_apply(c96):
+    # BF16 storage of every V-cycle matrix: the staged level-1 sweeps and the sliced-ELL
+    # interpolation and restriction in BF16 run at this size; bounds as in test_gpu_mixed.py
+    import paper_2505_18576_gb300 as m
+    p, o = c96
+    s = m.Solver(p.K, p.J, p.D, precision=3)
+    try:
+        assert int(s.info.staged_levels) & 2
+        r = np.random.default_rng(7).standard_normal(p.n)
+        out = {}
+        for f in ("vcycle", "apply"):
+            x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+            getattr(s, f)(torch.from_numpy(r).cuda(), x)
+            torch.cuda.synchronize()
+            out[f] = x.cpu().numpy()
+        xo = o.vcycle(r)
+        zo = o.apply(r)
+        ev = np.linalg.norm(out["vcycle"] - xo) / np.linalg.norm(xo)
+        ea = np.linalg.norm(out["apply"] - zo) / np.linalg.norm(zo)
+        print(f"c96 BF16: V-cycle rel diff {ev:.2e}, apply rel diff {ea:.2e}")
+        assert ev <= 5e-2 and ea <= 4e-2
+    finally:
+        s.close()
 
 
 @pytest.fixture(scope="module")

@@ -546,11 +546,11 @@ __global__ void __launch_bounds__(TPB) bsr3_kernel(BsrArgs a) {
       a2 = fma(m[6], x0, a2); a2 = fma(m[7], x1, a2); a2 = fma(m[8], x2, a2);
     };
     int64_t j = 0;
-    // A p with its dot product and r1 = r - A y1: two blocks' values loaded together; the other
-    // epilogues one block at a time, unrolled by 4.  Each form was the faster one for its
-    // epilogue on GB300 at c160 (A p 1875 -> 1740 us, post-smoother 1935 -> 1783 us against the
-    // earlier single loop unrolled by 2); the FMAs run in the same order in every form.
-    if (DOT || MODE == M_RESID_W) {
+    // A p with its dot product: two blocks' values loaded together; the other epilogues one block
+    // at a time, unrolled by 4.  Each form was the faster one for its epilogue on GB300 at c160
+    // (A p 1875 -> 1740 us, post-smoother 1935 -> 1783 us, r1 = r - A y1 1942 -> 1762 us against
+    // the earlier single loop unrolled by 2); the FMAs run in the same order in every form.
+    if (DOT) {
       for (; j + 1 < w; j += 2) {
         const int64_t J0 = __ldg(ci + 32 * j), J1 = __ldg(ci + 32 * j + 32);
         const double* p = vb + 288 * j;

@@ -42,7 +42,10 @@ typedef enum {
   AMGF_ERR_NOT_SPD = 3,      /* D_r <= 0, non-positive pivot in the coarse or filter factor */
   AMGF_ERR_BREAKDOWN = 4,    /* p^T A p <= 0 or r^T z <= 0 during PCG */
   AMGF_ERR_NOT_CONVERGED = 5,/* maxit reached; x holds the last iterate */
-  AMGF_ERR_CUDA = 6,         /* CUDA runtime error or no device */
+  AMGF_ERR_CUDA = 6,         /* CUDA runtime error or no device; also a device-side wait of the
+                                staged sweeps that gave up after 4 s (the kernel sets a flag and
+                                returns instead of hanging; amgf_pcg_solve and amgf_time_kernel
+                                read the flag, which stays set for the handle) */
   AMGF_ERR_OOM = 7           /* device or host allocation failed */
 } amgf_status;
 

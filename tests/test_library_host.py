@@ -225,12 +225,15 @@ def test_host_filter_solve_matches_oracle(case, algo):
 
 
 def test_staged_sweep_options_rejected():
-    # stage_rows in [0, 4096], stage_depth in [2, 8] when staging is on; checked before any device use
+    # stage_rows in [0, 4096], stage_depth in [2, 8] when staging is on, sell_window >= 0; checked
+    # before any device use
     p = cg.make_problem(None, seed=0, nx=4, ny=4, nz=2, d_lo=-2, d_hi=2)
     for kw in (dict(stage_rows=-1), dict(stage_rows=5000), dict(stage_rows=32, stage_depth=1),
-               dict(stage_rows=32, stage_depth=9)):
+               dict(stage_rows=32, stage_depth=9), dict(sell_window=-1)):
         with pytest.raises(amgf.AmgfError) as e:
             amgf.Solver(p.K, p.J, p.D, precision=3, host_only=True, **kw)
         assert e.value.status == 1
+    # the binding's struct ends where the C struct ends: the last fields read back their defaults
     o = amgf.amgf_options_default()
-    assert (o.stage_rows, o.stage_depth) == (32, 2)
+    assert (o.stage_rows, o.stage_depth, o.sell_window) == (32, 2, 256)
+    assert o.cheby_lower == 0.3

@@ -237,3 +237,22 @@ def test_staged_sweep_options_rejected():
     o = amgf.amgf_options_default()
     assert (o.stage_rows, o.stage_depth, o.sell_window) == (32, 2, 256)
     assert o.cheby_lower == 0.3
+
+
+@pytest.mark.parametrize("cname,pyname", [("amgf_options", "Options"), ("amgf_stats", "Stats"),
+                                          ("amgf_info", "Info")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    # the ctypes mirrors of the ABI structs list the header's fields in the header's order
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "amgf.h")).read()
+    body = hdr[:hdr.index("} " + cname + ";")]
+    body = body[body.rindex("typedef struct {") + len("typedef struct {"):]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "type a, b, c" declares several fields
+        names = decl.split(None, 1)[1]
+        fields += [re.sub(r"\[.*\]", "", x).strip() for x in names.split(",")]
+    assert [f[0] for f in getattr(amgf, pyname)._fields_] == fields

@@ -5,17 +5,41 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/amgf.h"
 
 namespace amgf {
 
+// Allocator whose value-less resize leaves the new elements uninitialised: the large CSR
+// arrays of the setup are sized first and then written in parallel, so the pages are first
+// touched by the threads that write them instead of by one serial zero-fill.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  using value_type = T;
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() noexcept = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+
 struct HCSR {
   int64_t nrows = 0, ncols = 0;
   std::vector<int64_t> rp;   // nrows + 1
-  std::vector<int32_t> ci;
-  std::vector<double> v;
+  std::vector<int32_t, NoInitAlloc<int32_t>> ci;  // resize() leaves entries unset: write them all
+  std::vector<double, NoInitAlloc<double>> v;
   int64_t nnz() const { return rp.empty() ? 0 : rp.back(); }
 };
 

@@ -94,40 +94,59 @@ HCSR transpose(const HCSR& a) {
   return t;
 }
 
-// C = A B; entry (i, J) accumulates a_ij b_jJ over row i of A in ascending j.
+// C = A B; entry (i, J) accumulates a_ij b_jJ over row i of A in ascending j.  Two passes over
+// row blocks: the row lengths (distinct columns, marked with the row as a stamp), then the values
+// accumulated in a dense row buffer and written straight into C's arrays, columns ascending.
 HCSR spgemm(const HCSR& a, const HCSR& b) {
   const int parts = std::max(1, nthreads() * 4);
   auto bounds = split_rows(a.nrows, parts);
-  RowPieces pc(parts);
+  HCSR c;
+  c.nrows = a.nrows;
+  c.ncols = b.ncols;
+  c.rp.assign(a.nrows + 1, 0);
+#pragma omp parallel
+  {
+    std::vector<int64_t> mark(b.ncols, -1);
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < parts; ++t)
+      for (int64_t i = bounds[t]; i < bounds[t + 1]; ++i) {
+        int64_t len = 0;
+        for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+          const int64_t j = a.ci[k];
+          for (int64_t kk = b.rp[j]; kk < b.rp[j + 1]; ++kk) {
+            const int32_t J = b.ci[kk];
+            if (mark[J] != i) { mark[J] = i; ++len; }
+          }
+        }
+        c.rp[i + 1] = len;
+      }
+  }
+  for (int64_t i = 0; i < a.nrows; ++i) c.rp[i + 1] += c.rp[i];
+  c.ci.resize(c.rp[a.nrows]);
+  c.v.resize(c.rp[a.nrows]);
 #pragma omp parallel
   {
     std::vector<double> acc(b.ncols, 0.0);
     std::vector<int64_t> mark(b.ncols, -1);
-    std::vector<int32_t> cols;
 #pragma omp for schedule(dynamic, 1)
-    for (int t = 0; t < parts; ++t) {
-      auto& L = pc.len[t];
-      auto& C = pc.ci[t];
-      auto& V = pc.v[t];
+    for (int t = 0; t < parts; ++t)
       for (int64_t i = bounds[t]; i < bounds[t + 1]; ++i) {
-        cols.clear();
+        int32_t* cols = c.ci.data() + c.rp[i];
+        int64_t n = 0;
         for (int64_t k = a.rp[i]; k < a.rp[i + 1]; ++k) {
           const int64_t j = a.ci[k];
           const double aij = a.v[k];
           for (int64_t kk = b.rp[j]; kk < b.rp[j + 1]; ++kk) {
             const int32_t J = b.ci[kk];
-            if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; cols.push_back(J); }
+            if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; cols[n++] = J; }
             acc[J] += aij * b.v[kk];
           }
         }
-        std::sort(cols.begin(), cols.end());
-        L.push_back((int64_t)cols.size());
-        for (int32_t J : cols) { C.push_back(J); V.push_back(acc[J]); }
+        std::sort(cols, cols + n);
+        double* vals = c.v.data() + c.rp[i];
+        for (int64_t q = 0; q < n; ++q) vals[q] = acc[cols[q]];
       }
-    }
   }
-  HCSR c;
-  pc.gather(c, a.nrows, b.ncols);
   return c;
 }
 

@@ -535,9 +535,10 @@ def run_gpu(args, rank, world, local):
 def kernel_source_sha(kind: str = "fine", precision: int = 0):
     """Hash of the source a roofline kernel is built from: the fine-level FP64 BSR3 kernel
     (kind "fine", precision 0) or the mixed one (precision 1-3) with the host code that lays its
-    operator out, or the CSR level kernel with the host setup that builds the coarse levels
-    (kind "level1").  DRAM traffic stored in profiles/roofline_traffic.json is used only while
-    this hash is unchanged."""
+    operator out, or the level-1 kernels (CSR, sliced ELL, staged) with the host code that
+    chooses and lays out their operators (kind "level1"; the hierarchy itself is pinned bit for
+    bit to the oracle by the CPU tests).  DRAM traffic stored in profiles/roofline_traffic.json
+    is used only while this hash is unchanged."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2505_18576_gb300", "csrc")
@@ -551,7 +552,8 @@ def kernel_source_sha(kind: str = "fine", precision: int = 0):
         h.update(a[i:a.index("static int grid_for(", i)].encode())
         i = a.index("static int upload_csr(")
         h.update(a[i:a.index("static void fill_info(", i)].encode())
-        h.update(c.encode())
+        i = c.index("void build_sell(")
+        h.update(c[i:c.index("bool build_bsr3(", i)].encode())
         return h.hexdigest()[:12]
     mid = k.index("// Fine level of the FP32 V-cycle")
     if precision == 0:

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <queue>
 #include <utility>
 
@@ -189,7 +190,46 @@ void strength_graph(const HCSR& A, const std::vector<int32_t>& func, double thet
   }
 }
 
-// Ruge-Stueben first pass with a lazy max-heap keyed by (measure, -index).
+// Subset of [0, n) with insert, erase and smallest element: a tree of 64-bit words, each bit of
+// a level summarising one word of the level below.
+struct MinSet {
+  std::vector<std::vector<uint64_t>> lv;  // lv[0]: one bit per element
+  explicit MinSet(int64_t n) {
+    int64_t m = n;
+    do {
+      m = (m + 63) / 64;
+      lv.emplace_back(m, 0);
+    } while (m > 1);
+  }
+  void insert(int64_t i) {
+    for (auto& w : lv) {
+      uint64_t& x = w[i >> 6];
+      const bool had = x != 0;
+      x |= 1ull << (i & 63);
+      if (had) return;
+      i >>= 6;
+    }
+  }
+  void erase(int64_t i) {
+    for (auto& w : lv) {
+      uint64_t& x = w[i >> 6];
+      x &= ~(1ull << (i & 63));
+      if (x) return;
+      i >>= 6;
+    }
+  }
+  bool empty() const { return lv.back()[0] == 0; }
+  int64_t min() const {
+    int64_t i = 0;
+    for (int k = (int)lv.size() - 1; k >= 0; --k) i = (i << 6) | __builtin_ctzll(lv[k][i]);
+    return i;
+  }
+};
+
+// Ruge-Stueben first pass: repeatedly the undecided point of largest measure (ties: smallest
+// index) becomes C.  Measures are small integers that change by one, so the undecided points sit
+// in one MinSet per measure value and the current largest measure is tracked; a point whose
+// measure reaches 0 can never be chosen (no undecided or F point depends on it any more).
 std::vector<int8_t> ruge_stueben(int64_t n, const std::vector<int64_t>& srp, const std::vector<int32_t>& sci) {
   // dependents: transpose of the strength pattern
   std::vector<int64_t> trp(n + 1, 0);
@@ -204,29 +244,52 @@ std::vector<int8_t> ruge_stueben(int64_t n, const std::vector<int64_t>& srp, con
   enum : int8_t { UND = 0, FPT = 1, CPT = 2 };
   std::vector<int8_t> state(n, UND);
   std::vector<int64_t> lam(n);
-  using Key = std::pair<int64_t, int64_t>;  // (measure, -index): top = largest measure, smallest index
-  std::vector<Key> init(n);
-  for (int64_t i = 0; i < n; ++i) { lam[i] = trp[i + 1] - trp[i]; init[i] = Key(lam[i], -i); }
-  std::priority_queue<Key> heap(std::less<Key>(), std::move(init));
-  while (!heap.empty()) {
-    const Key top = heap.top();
-    heap.pop();
-    const int64_t i = -top.second;
-    if (state[i] != UND || lam[i] != top.first) continue;  // stale entry
-    if (top.first <= 0) break;
+  int64_t top = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    lam[i] = trp[i + 1] - trp[i];
+    top = std::max(top, lam[i]);
+  }
+  // a measure is |S^T_i among undecided| + 2 |S^T_i among F| <= 2 |S^T_i|
+  std::vector<std::unique_ptr<MinSet>> bucket(2 * top + 2);
+  auto put = [&](int64_t i) {
+    const int64_t m = lam[i];
+    if (m < 1) return;
+    if (!bucket[m]) bucket[m].reset(new MinSet(n));
+    bucket[m]->insert(i);
+  };
+  auto take = [&](int64_t i) {
+    if (lam[i] >= 1) bucket[lam[i]]->erase(i);
+  };
+  for (int64_t i = 0; i < n; ++i) put(i);
+  int64_t cur = top;
+  for (;;) {
+    while (cur >= 1 && (!bucket[cur] || bucket[cur]->empty())) --cur;
+    if (cur < 1) break;
+    const int64_t i = bucket[cur]->min();
+    take(i);
     state[i] = CPT;
     for (int64_t k = trp[i]; k < trp[i + 1]; ++k) {
       const int32_t j = tci[k];
       if (state[j] != UND) continue;
+      take(j);
       state[j] = FPT;
       for (int64_t kk = srp[j]; kk < srp[j + 1]; ++kk) {
         const int32_t q = sci[kk];
-        if (state[q] == UND) { lam[q] += 1; heap.push(Key(lam[q], -(int64_t)q)); }
+        if (state[q] == UND) {
+          take(q);
+          lam[q] += 1;
+          put(q);
+          cur = std::max(cur, lam[q]);
+        }
       }
     }
     for (int64_t k = srp[i]; k < srp[i + 1]; ++k) {
       const int32_t q = sci[k];
-      if (state[q] == UND) { lam[q] -= 1; heap.push(Key(lam[q], -(int64_t)q)); }
+      if (state[q] == UND) {
+        take(q);
+        lam[q] -= 1;
+        put(q);
+      }
     }
   }
   std::vector<int8_t> cf(n);

@@ -1430,7 +1430,7 @@ static int update_D_in_place(Ctx& c, const double* D, const amgf_csr& K, const a
     const int64_t tot = F2.nb * F2.nblk;
     if (F2.algo == 0) {
       if ((st = copy_to_device(c.fM, F2.M.data(), (int64_t)F2.M.size()))) return st;
-      std::vector<double>().swap(F2.M);
+      decltype(F2.M)().swap(F2.M);
     } else {
       if ((st = copy_to_device(c.fG, F2.G.data(), tot * F2.nb))) return st;
       if ((st = copy_to_device(c.fGT, F2.GT.data(), tot * F2.nb))) return st;
@@ -1675,7 +1675,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       if ((st = c.upload(&c.fM, c.F.M.data(), (int64_t)c.F.M.size()))) return st;
       c.fM_count = (int64_t)c.F.M.size();
       if ((st = c.upload(&c.ftasks, c.F.tasks.data(), (int64_t)c.F.tasks.size()))) return st;
-      std::vector<double>().swap(c.F.M);  // the device copy is the only one used
+      decltype(c.F.M)().swap(c.F.M);  // the device copy is the only one used
       if (2 * c.F.nb * (int64_t)sizeof(double) > 48 * 1024) {
         const int bytes = (int)(2 * c.F.nb * sizeof(double));
         CK(cudaFuncSetAttribute(filter_bcr_kernel<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));

@@ -646,18 +646,54 @@ int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<dou
   }
   std::vector<double>().swap(Ad);
   std::vector<double>().swap(As);
-  F.M.clear();
-  auto push = [&](const std::vector<double>& m) {
-    const int64_t idx = (int64_t)(F.M.size() / bsz);
-    F.M.insert(F.M.end(), m.begin(), m.end());
-    return idx;
+  // F.M holds every matrix the solve applies, in the order the reduction produces them: per
+  // level, for each block k, an odd block's A_k^{-1}, F_{k-1}^T and (if k + 1 < N) E_{k+1}^T,
+  // an even block's E_k (k >= 1) and F_k (k + 1 < N); the inverse of the last block at the end.
+  // The count is known in advance, so F.M is sized once and each level's matrices are copied
+  // into their slots in parallel.
+  auto level_count = [](int64_t n) {
+    int64_t c = 0;
+    for (int64_t k = 0; k < n; ++k) c += (k & 1) ? 2 + (k + 1 < n) : (k >= 1) + (k + 1 < n);
+    return c;
+  };
+  int64_t total = 1;
+  for (int64_t n = nblk; n > 1; n = (n + 1) / 2) total += level_count(n);
+  F.M.resize(total * bsz);
+  int64_t next = 0;
+  struct Slot {
+    const std::vector<double>* m;
+    bool transposed;
+  };
+  std::vector<Slot> slots;  // matrices of the current level, slot next - slots.size() + i
+  auto push = [&](const std::vector<double>& m, bool transposed) {
+    slots.push_back({&m, transposed});
+    return next++;
+  };
+  auto flush = [&]() {
+    const int64_t first = next - (int64_t)slots.size();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < (int64_t)slots.size(); ++q) {
+      double* dst = F.M.data() + (first + q) * bsz;
+      const double* src = slots[q].m->data();
+      if (!slots[q].transposed) {
+        std::copy(src, src + bsz, dst);
+      } else {
+        for (int64_t i = 0; i < nb; ++i)
+          for (int64_t j = 0; j < nb; ++j) dst[j * nb + i] = src[i * nb + j];
+      }
+    }
+    slots.clear();
   };
   std::vector<std::vector<FilterTask>> fwd, bwd;
   bool spd = true;
   while (N > 1) {
     std::vector<std::vector<double>> Ainv(N), E(N), Fk(N), R(N);
+    // With fewer blocks than threads (the top levels of the reduction) the blocks run one after
+    // another and each block's dense kernels run in parallel instead; the arithmetic of every
+    // entry is the same either way.
+    const bool by_block = N / 2 >= nthreads();
     // odd blocks: Cholesky factors R_k (A_k = R_k R_k^T) and the inverses the solve applies
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if (by_block)
     for (int64_t k = 1; k < N; k += 2) {
       std::vector<double> r = A[k];
       std::vector<double> inv;
@@ -677,7 +713,7 @@ int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<dou
     // F_k = W2 R_{k+1}^{-1}, L'_k = -E_k L_{k-1}
     const int64_t N2 = (N + 1) / 2;
     std::vector<std::vector<double>> A2(N2), L2(N2);
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) if (by_block)
     for (int64_t k = 0; k < N; k += 2) {
       std::vector<double> a = A[k], w(bsz), wt;
       if (k >= 1) {
@@ -710,17 +746,18 @@ int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<dou
     for (int64_t k = 0; k < N; ++k) {
       const int32_t o = (int32_t)(k * stride);
       if (k & 1) {
-        tf.push_back({push(Ainv[k]), -1, o, o, -1, 0});
-        const int64_t mb = push(transpose_block(nb, Fk[k - 1]));
-        const int64_t mc = k + 1 < N ? push(transpose_block(nb, E[k + 1])) : -1;
+        tf.push_back({push(Ainv[k], false), -1, o, o, -1, 0});
+        const int64_t mb = push(Fk[k - 1], true);
+        const int64_t mc = k + 1 < N ? push(E[k + 1], true) : -1;
         tb.push_back({mb, mc, o, (int32_t)((k - 1) * stride), k + 1 < N ? (int32_t)((k + 1) * stride) : -1, 2});
       } else {
-        const int64_t me = k >= 1 ? push(E[k]) : -1;
-        const int64_t mf = k + 1 < N ? push(Fk[k]) : -1;
+        const int64_t me = k >= 1 ? push(E[k], false) : -1;
+        const int64_t mf = k + 1 < N ? push(Fk[k], false) : -1;
         tf.push_back({me, mf, o, k >= 1 ? (int32_t)((k - 1) * stride) : -1,
                       k + 1 < N ? (int32_t)((k + 1) * stride) : -1, 1});
       }
     }
+    flush();
     fwd.push_back(std::move(tf));
     bwd.push_back(std::move(tb));
     A.swap(A2);
@@ -730,7 +767,9 @@ int build_bcr(int64_t nb, int64_t nblk, std::vector<double>& Ad, std::vector<dou
   }
   std::vector<double> inv0;
   if (!spd_inverse(A[0], nb, inv0)) { err = "filter matrix A_w is not SPD"; return AMGF_ERR_NOT_SPD; }
-  const int64_t m0 = push(inv0);
+  const int64_t m0 = push(inv0, false);
+  flush();
+  if (next != total) { err = "filter factor count mismatch"; return AMGF_ERR_INVALID_ARG; }
   F.bcr_levels = (int)fwd.size();
   F.tasks.clear();
   F.phase_off.assign(1, 0);

@@ -77,7 +77,7 @@ struct Filter {
   // algo 0: odd-even block cyclic reduction; matrices nb x nb row-major in M, one task list
   // per phase: phases 0..L-1 reduce level 0..L-1, phase L solves the last block, phases
   // L+1..2L substitute back through levels L-1..0
-  std::vector<double> M;
+  std::vector<double, NoInitAlloc<double>> M;  // sized once, every entry written
   std::vector<FilterTask> tasks;
   std::vector<int64_t> phase_off; // tasks of phase q: [phase_off[q], phase_off[q+1])
   int bcr_levels = 0;             // L

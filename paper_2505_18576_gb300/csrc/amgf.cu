@@ -1499,7 +1499,7 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
       t_assemble = since(t_start);
       t1 = std::chrono::steady_clock::now();
     }
-    st = build_hierarchy(S, c.o, c.H, err);
+    st = build_hierarchy(std::move(S), c.o, c.H, err);  // S is not used again
     if (st) return fail(st, err);
   }
   if (c.m > 0) c.Dh.assign(D, D + c.m);

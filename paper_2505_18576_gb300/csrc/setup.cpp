@@ -1069,15 +1069,16 @@ int refresh_contact_rows(HCSR& S, const amgf_csr* K, const amgf_csr* J, const do
   return AMGF_OK;
 }
 
-int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::string& err) {
+int build_hierarchy(HCSR S, const amgf_options& o, Hierarchy& H, std::string& err) {
   H = Hierarchy();
   double t_str = 0, t_rs = 0, t_int = 0, t_gal = 0;
   auto now = [] {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
   };
-  H.A.push_back(S);
-  H.func.emplace_back(S.nrows);
-  for (int64_t i = 0; i < S.nrows; ++i) H.func[0][i] = o.num_functions > 1 ? (int32_t)(i % o.num_functions) : 0;
+  const int64_t n0 = S.nrows;
+  H.A.push_back(std::move(S));  // A_0 takes the caller's matrix (moved in by callers that are done with it)
+  H.func.emplace_back(n0);
+  for (int64_t i = 0; i < n0; ++i) H.func[0][i] = o.num_functions > 1 ? (int32_t)(i % o.num_functions) : 0;
   int l = 0;
   for (;;) {
     const HCSR& A = H.A[l];

@@ -163,7 +163,7 @@ int add_diagonal(HCSR& A, const double* E, std::string& err);
 
 // B := AMG(A): strength, Ruge-Stueben first pass, direct interpolation, Galerkin, l1 sums,
 // dense inverse of the coarsest level.
-int build_hierarchy(const HCSR& S, const amgf_options& o, Hierarchy& H, std::string& err);
+int build_hierarchy(HCSR S, const amgf_options& o, Hierarchy& H, std::string& err);
 
 // Features of the learned smoother for every smoothed level (6 per row, row-major):
 //   log10(a_ii)/10, log10(l1_i)/10, a_ii/l1_i, contact flag, log10(1 + d_i)/10, l/(nlev-1),

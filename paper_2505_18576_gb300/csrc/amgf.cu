@@ -1773,11 +1773,20 @@ static int build_all(Ctx& c, const double* D, bool keep_coarse = false) {
   return AMGF_OK;
 }
 
+// Host copy of a caller's CSR matrix (kept by the handle); the large arrays are sized without
+// a fill and copied in parallel chunks.
 static void copy_csr(const amgf_csr* a, HCSR& h) {
   h.nrows = a->nrows; h.ncols = a->ncols;
   h.rp.assign(a->row_ptr, a->row_ptr + a->nrows + 1);
-  h.ci.assign(a->col_idx, a->col_idx + a->nnz);
-  h.v.assign(a->val, a->val + a->nnz);
+  h.ci.resize(a->nnz);
+  h.v.resize(a->nnz);
+  const int64_t chunk = 1 << 20, nchunk = (a->nnz + chunk - 1) / chunk;
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < nchunk; ++q) {
+    const int64_t b = q * chunk, e = std::min(a->nnz, b + chunk);
+    std::copy(a->col_idx + b, a->col_idx + e, h.ci.begin() + b);
+    std::copy(a->val + b, a->val + e, h.v.begin() + b);
+  }
 }
 
 // join the caller's stream: library stream waits for it (begin) / caller waits for us (end)
